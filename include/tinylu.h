@@ -1,0 +1,222 @@
+/*
+ * tinylu.h -- C ABI of the GB300 (sm_103a) tiny batched LU library.
+ *
+ * Solves very large batches of independent general dense systems
+ * A_s x_s = b_s of dimension n <= 32 in IEEE binary64 by LU factorization
+ * with partial pivoting (LUpp): PA = LU, then Ly = Pb and Ux = y
+ * (paper Sec. 2.2).  The same solvers run inside a fused kernel that carries
+ * each integration point's own Newton loop (paper Sec. 2.1 Eqs. 1-3 and
+ * Algorithm 2).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every data pointer is a DEVICE pointer owned by the caller unless the
+ *    call's comment says otherwise.  The library never frees caller memory.
+ *  - Calls are asynchronous on `stream` (NULL = legacy default stream).
+ *    Argument errors are detected on the host before any launch and return
+ *    TL_ERR_INVALID_ARG synchronously; tl_last_bad_arg() then gives the
+ *    1-based position of the offending argument, LAPACK style.  Nothing is
+ *    thrown across the ABI.  A CUDA launch error returns TL_ERR_CUDA and
+ *    tl_last_cuda_error() gives the cudaError_t value.
+ *  - A handle is not thread-safe: use one handle per host thread.
+ *  - Matrix entry (i,j) of system s (0-based) is stored
+ *      TL_LAYOUT_PER_SYSTEM : A[s*n*n + j*n + i]   (column-major per system,
+ *                                                    LAPACK convention of the
+ *                                                    batched solvers, Sec. 3.1)
+ *      TL_LAYOUT_INTERLEAVED: A[(j*n + i)*ld + s]   (batch-minor: consecutive
+ *                                                    systems adjacent, the
+ *                                                    coalescing layout of
+ *                                                    Sec. 2.3)
+ *    Vectors (b, x, one right-hand side) are b[s*n + i] or b[i*ld + s];
+ *    pivots ipiv[s*n + k] or ipiv[k*ld + s]; info is always info[s].
+ *    `ld` (ld_batch) must be >= batch for the interleaved layout and is
+ *    ignored for the per-system layout.  All device pointers must be
+ *    8-byte aligned (4-byte for int32 arrays).
+ *  - Pivots follow LAPACK: ipiv[k] (1-based) is the row interchanged with
+ *    row k at elimination step k.  The pivot row is the FIRST row of largest
+ *    magnitude in the column (ties go to the smallest current row index).
+ *  - Per-system info: 0 success; k+1 if the pivot of step k is exactly zero
+ *    (the factorization still completes, no solve is attempted and x is set
+ *    to NaN); -1 if an entry of A is NaN or +-Inf (nothing is factored,
+ *    ipiv is the identity and x is NaN).
+ *  - Arithmetic is binary64 throughout the factorization with one rounding
+ *    per operation: multipliers l_ik = a_ik * RN(1/a_kk) (a_ik / a_kk when
+ *    |a_kk| < DBL_MIN) and Schur updates fma(-l_ik, u_kj, a_ij), so the LU
+ *    factors and the pivots are bit-identical to a sequential textbook
+ *    right-looking elimination with those operations.
+ */
+#ifndef TINYLU_H
+#define TINYLU_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TL_MAX_N 32
+
+typedef struct tl_handle tl_handle;
+
+typedef enum {
+    TL_OK = 0,
+    TL_ERR_INVALID_ARG = -1,   /* see tl_last_bad_arg()                     */
+    TL_ERR_CUDA = -2,          /* see tl_last_cuda_error()                  */
+    TL_ERR_NO_MEMORY = -3,     /* workspace could not be allocated          */
+    TL_ERR_UNSUPPORTED = -4,   /* valid request this build does not serve   */
+    TL_ERR_TIMEOUT = -5        /* a bounded device wait gave up             */
+} tl_status;
+
+typedef enum { TL_LAYOUT_PER_SYSTEM = 0, TL_LAYOUT_INTERLEAVED = 1 } tl_layout;
+
+typedef enum { TL_PREC_FP64 = 0, TL_PREC_FP32_IR = 1 } tl_precision;
+
+typedef enum { TL_LAW_NORTON = 0, TL_LAW_TANH = 1 } tl_law_id;
+
+/* Per-point Newton status codes written by tl_newton_integrate. */
+enum {
+    TL_NEWTON_CONVERGED = 0,
+    TL_NEWTON_MAX_ITER = 1,
+    TL_NEWTON_SINGULAR = 2,
+    TL_NEWTON_NONFINITE = 3
+};
+
+/*
+ * Constitutive law descriptor for tl_newton_integrate.
+ *   TL_LAW_NORTON: n must be 7; params = {E, nu, A, m, dt} (m a positive
+ *     integer stored as double).  Implicit Euler of an isotropic-elastic,
+ *     J2, Norton-viscoplastic law (the law class of Sec. 4.3); unknowns
+ *     x = (de_el[6] in Mandel notation, dp).
+ *   TL_LAW_TANH: n in 1..32; F(x) = A x + c .* tanh(x) - b per point;
+ *     params unused.
+ */
+typedef struct {
+    int32_t id;
+    int32_t n;
+    double params[6];
+} tl_law;
+
+/* Create a handle on the current CUDA device.  Allocates no device memory. */
+tl_status tl_create(tl_handle **h);
+
+/* Destroy a handle and release the workspace it owns (synchronizes it). */
+tl_status tl_destroy(tl_handle *h);
+
+/* Static, human-readable name of a status code.  Never NULL. */
+const char *tl_status_string(tl_status s);
+
+/* cudaError_t of the last TL_ERR_CUDA on this handle (0 if none). */
+tl_status tl_last_cuda_error(tl_handle *h, int *err);
+
+/* 1-based position of the argument rejected by the last TL_ERR_INVALID_ARG
+ * on this handle (0 if none). */
+int tl_last_bad_arg(tl_handle *h);
+
+/*
+ * tl_getrf_batched -- LUpp factorization in place (Sec. 2.2, PA = LU).
+ *   n      1..32
+ *   A      in: the batch of matrices; out: L (unit lower, strictly below the
+ *          diagonal) and U, LAPACK getrf storage, in the given layout.
+ *   ipiv   out: n pivots per system (same layout rules as a vector, int32).
+ *   info   out: one int32 per system, see the conventions above.
+ *   batch  >= 0 (0 is a no-op).
+ */
+tl_status tl_getrf_batched(tl_handle *h, int n, double *A, tl_layout layout, int64_t ld_batch,
+                           int32_t *ipiv, int32_t *info, int64_t batch, cudaStream_t stream);
+
+/*
+ * tl_getrs_batched -- solve with the factors of tl_getrf_batched
+ * (Sec. 2.2: Ly = Pb, Ux = y).
+ *   nrhs   1..32 right-hand sides per system.
+ *   LU, ipiv  as written by tl_getrf_batched (not modified).
+ *   B      in: right-hand sides, out: solutions.  Per-system layout:
+ *          B[s*n*nrhs + r*n + i] (column-major n x nrhs); interleaved:
+ *          B[(r*n + i)*ld + s].
+ *   Systems with a zero pivot produce Inf/NaN as the arithmetic gives
+ *   (LAPACK getrs does not test for singularity either).
+ */
+tl_status tl_getrs_batched(tl_handle *h, int n, int nrhs, const double *LU, const int32_t *ipiv,
+                           tl_layout layout, int64_t ld_batch, double *B, int64_t batch,
+                           cudaStream_t stream);
+
+/*
+ * tl_gesv_batched -- fused factor + solve for one right-hand side
+ * (Sec. 3.1, the gesv form of the batched solvers; the elimination carries b
+ * along as an extra column so that Ly = Pb is formed during the
+ * factorization).
+ *   A       in, not modified.
+ *   LU_out  nullable; if not NULL receives the getrf factors.
+ *   b       in, not modified.  x out (may alias b).
+ *   ipiv, info  out.
+ * The back substitution multiplies by the reciprocals RN(1/u_ii) formed
+ * during the factorization instead of dividing by u_ii; x therefore agrees
+ * with a dividing substitution to within a few units in the last place per
+ * step (well inside the normwise backward-error bound), while LU, ipiv and
+ * the forward-substituted y are bit-identical to the sequential algorithm.
+ */
+tl_status tl_gesv_batched(tl_handle *h, int n, const double *A, double *LU_out, const double *b,
+                          double *x, int32_t *ipiv, int32_t *info, tl_layout layout,
+                          int64_t ld_batch, int64_t batch, cudaStream_t stream);
+
+/*
+ * tl_lupp_solve_batched -- ragged batch: system s has its own size n[s]
+ * (1..32) and lives anywhere in the A / b / ipiv arrays (per-system
+ * column-major storage at the given element offsets).
+ *   n       device int32[batch]
+ *   a_off   device int64[batch]: A_s starts at A + a_off[s]
+ *   b_off   device int64[batch]: b_s at b + b_off[s] and x_s at x + b_off[s]
+ *   piv_off device int64[batch]: ipiv_s at ipiv + piv_off[s]
+ *   info    device int32[batch]
+ *   prec    TL_PREC_FP64 (factor in binary64), or TL_PREC_FP32_IR (factor
+ *           in binary32, refine residual and correction in binary64; see
+ *           refine_steps)
+ *   refine_steps  nullable device int32[batch]: refinement steps taken
+ *           (FP32_IR), -1 when the system fell back to a binary64 factor.
+ * Systems are bucketed by n on the device (handle workspace) and solved by
+ * the per-n kernels of tl_gesv_batched.
+ */
+tl_status tl_lupp_solve_batched(tl_handle *h, int64_t batch, const int32_t *n, const int64_t *a_off,
+                                const double *A, const int64_t *b_off, const double *b, double *x,
+                                const int64_t *piv_off, int32_t *ipiv, int32_t *info,
+                                tl_precision prec, int32_t *refine_steps, cudaStream_t stream);
+
+/*
+ * tl_newton_integrate -- one fused kernel runs every point's own Newton loop
+ * (Algorithm 2; Eqs. 1-3 of Sec. 2.1): assemble F and J, solve
+ * J dx = -F by the in-register LUpp, x += dx, test convergence.
+ *   law      law descriptor (host pointer, read during the call).
+ *   inputs   per-point law data, field-major with stride npoints
+ *            (inputs[f*npoints + p]):
+ *              Norton: f = 0..5 sig0 (Mandel), f = 6..11 deps (Mandel);
+ *              tanh  : f = 0..n*n-1 A column-major, then c (n), then b (n).
+ *   x        out: final unknowns, x[i*npoints + p].  The initial guess is
+ *            the law's own (Norton: the elastic predictor (deps, 0);
+ *            tanh: 0).
+ *   outputs  nullable; Norton: end-of-step stress sig[i*npoints + p].
+ *   iterations, status  int32[npoints]: linear solves performed and the
+ *            TL_NEWTON_* code.
+ *   rtol     stop when ||F(x_k)||_2 <= rtol * ||F(x_0)||_2 (or F(x_0) = 0).
+ *   max_iter at most this many linear solves (>= 0).
+ */
+tl_status tl_newton_integrate(tl_handle *h, const tl_law *law, int64_t npoints,
+                              const double *inputs, double *x, double *outputs,
+                              int32_t *iterations, int32_t *status, double rtol, int max_iter,
+                              cudaStream_t stream);
+
+/*
+ * tl_autotune -- time the candidate kernels (thread-to-system mapping and
+ * block size) for every n in [n_min, n_max] and the layout on the current
+ * device, and keep the fastest per n in the handle's dispatch table (the
+ * "best X" size-aware dispatcher, Sec. 4.1).  table_path nullable: if
+ * given, the table is also written there as JSON.  Allocates and frees a
+ * temporary device batch; must not run during stream capture.
+ */
+tl_status tl_autotune(tl_handle *h, int n_min, int n_max, tl_layout layout,
+                      const char *table_path);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TINYLU_H */
