@@ -1,0 +1,411 @@
+// tl_device.cuh -- device-callable tiny LUpp solvers for sm_103a.
+//
+// Two thread-to-system mappings (paper Sec. 2.3, "thread-to-system mapping"):
+//
+//   * lu_thread_*  -- one thread owns one system; the whole matrix lives in
+//     that thread's registers (single-threaded family of Sec. 3.2.2).  All
+//     loops are unrolled at compile time for the system size N, so every
+//     FP64 instruction issued does useful work on all 32 lanes.
+//
+//   * lu_group_*   -- T consecutive lanes own one system, lane t holding the
+//     rows i = t, t+T, t+2T, ... (K = ceil(N/T) row slots, round-robin so a
+//     column access stays coalesced, Sec. 3.2.1); slots past N are phantom
+//     rows skipped at compile time.  The pivot search is a butterfly
+//     __shfl_xor arg-max, the pivot row is broadcast with __shfl, and the
+//     physical row interchange is a register permutation between the two
+//     owning lanes.
+//
+// Arithmetic (identical in both mappings, and identical to the sequential
+// right-looking elimination of Sec. 2.2):
+//   pivot    p = first row i >= k of largest |a_ik|.  The magnitude compare is
+//            an integer compare of the IEEE bit pattern with the sign cleared,
+//            which orders finite values exactly as |x| does and keeps the
+//            search off the FP64 pipe.
+//   zero     a_pk == 0: info = k+1 (first), the step does nothing else.
+//   scale    l_ik = a_ik * RN(1/a_kk) (a_ik / a_kk when |a_kk| < DBL_MIN).
+//   update   a_ij = fma(-l_ik, a_kj, a_ij), every element updated once per
+//            step in increasing k, so the order of rounding is fixed.
+// Every FP64 operation is an explicit round-to-nearest intrinsic, so the
+// compiler cannot contract or reorder any of them.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tl {
+namespace dev {
+
+constexpr unsigned long long kMagMask = 0x7fffffffffffffffULL;
+constexpr unsigned long long kDblMinBits = 0x0010000000000000ULL;  // DBL_MIN
+constexpr unsigned long long kInfBits = 0x7ff0000000000000ULL;      // +Inf
+
+__device__ __forceinline__ unsigned long long mag_bits(double v)
+{
+    return static_cast<unsigned long long>(__double_as_longlong(v)) & kMagMask;
+}
+
+__device__ __forceinline__ bool is_nonfinite(double v) { return mag_bits(v) >= kInfBits; }
+
+__device__ __forceinline__ double nan_value() { return __longlong_as_double(0x7ff8000000000000LL); }
+
+// 64-bit select done on the integer pipe (two 32-bit selects).
+__device__ __forceinline__ double sel(bool c, double a, double b)
+{
+    long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    return __longlong_as_double(c ? ia : ib);
+}
+
+// ---------------------------------------------------------------------------
+// One thread per system, everything in registers.
+// ---------------------------------------------------------------------------
+
+// Returns true when any entry is NaN or +-Inf.
+template <int N>
+__device__ __forceinline__ bool any_nonfinite(const double (&a)[N][N])
+{
+    unsigned long long worst = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            unsigned long long m = mag_bits(a[i][j]);
+            worst = m > worst ? m : worst;
+        }
+    return worst >= kInfBits;
+}
+
+// In-register LUpp of a[i][j] (row i, column j).
+//   KEEP_L : also permute the already-computed multipliers (getrf output);
+//            without it the L part is left in elimination order, which is
+//            all a fused solve needs.
+//   NB     : number of right-hand-side columns eliminated along with A
+//            (forward substitution fused into the factorization).
+// piv[k] receives the 0-based pivot row, rcp[k] = RN(1/u_kk) (valid when
+// `tiny` stays false).  Returns info (0 or first zero pivot step + 1).
+template <int N, bool KEEP_L, int NB>
+__device__ __forceinline__ int lu_thread_factor(double (&a)[N][N], double (&b)[NB > 0 ? NB : 1][N],
+                                                int (&piv)[N], double (&rcp)[N], bool &tiny)
+{
+    int info = 0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        // a2: pivot search on the magnitude bit patterns (first maximum).
+        unsigned long long best = mag_bits(a[k][k]);
+        int p = k;
+#pragma unroll
+        for (int i = k + 1; i < N; ++i) {
+            unsigned long long m = mag_bits(a[i][k]);
+            bool gt = m > best;
+            best = gt ? m : best;
+            p = gt ? i : p;
+        }
+        piv[k] = p;
+        rcp[k] = 0.0;
+        if (best == 0ULL) {
+            if (info == 0) info = k + 1;
+            continue;
+        }
+        // a3: physical row interchange k <-> p as a register permutation.
+        const int j0 = KEEP_L ? 0 : k;
+#pragma unroll
+        for (int i = k + 1; i < N; ++i) {
+            const bool s = (p == i);
+#pragma unroll
+            for (int j = j0; j < N; ++j) {
+                double t = a[k][j];
+                a[k][j] = sel(s, a[i][j], t);
+                a[i][j] = sel(s, t, a[i][j]);
+            }
+#pragma unroll
+            for (int c = 0; c < NB; ++c) {
+                double t = b[c][k];
+                b[c][k] = sel(s, b[c][i], t);
+                b[c][i] = sel(s, t, b[c][i]);
+            }
+        }
+        // a4: multipliers with one correctly rounded reciprocal.
+        const double pv = a[k][k];
+        if (best >= kDblMinBits) {
+            const double r = __drcp_rn(pv);
+            rcp[k] = r;
+#pragma unroll
+            for (int i = k + 1; i < N; ++i) a[i][k] = __dmul_rn(a[i][k], r);
+        } else {
+            tiny = true;
+#pragma unroll
+            for (int i = k + 1; i < N; ++i) a[i][k] = __ddiv_rn(a[i][k], pv);
+        }
+        // a5: rank-1 Schur update; a6 (forward part): b follows as extra columns.
+#pragma unroll
+        for (int j = k + 1; j < N; ++j)
+#pragma unroll
+            for (int i = k + 1; i < N; ++i) a[i][j] = __fma_rn(-a[i][k], a[k][j], a[i][j]);
+#pragma unroll
+        for (int c = 0; c < NB; ++c)
+#pragma unroll
+            for (int i = k + 1; i < N; ++i) b[c][i] = __fma_rn(-a[i][k], b[c][k], b[c][i]);
+    }
+    return info;
+}
+
+// a6 (back part): x_i = (y_i - sum_{j>i} u_ij x_j) * RN(1/u_ii), the sum
+// accumulated in decreasing j.  y is overwritten by x.  When a pivot was
+// below DBL_MIN the reciprocal may overflow, so that case divides.
+template <int N>
+__device__ __forceinline__ void lu_thread_backsolve(const double (&a)[N][N], double (&y)[N],
+                                                    const double (&rcp)[N], bool tiny)
+{
+    if (!tiny) {
+#pragma unroll
+        for (int i = N - 1; i >= 0; --i) {
+            double s = y[i];
+#pragma unroll
+            for (int j = N - 1; j > i; --j) s = __fma_rn(-a[i][j], y[j], s);
+            y[i] = __dmul_rn(s, rcp[i]);
+        }
+    } else {
+#pragma unroll
+        for (int i = N - 1; i >= 0; --i) {
+            double s = y[i];
+#pragma unroll
+            for (int j = N - 1; j > i; --j) s = __fma_rn(-a[i][j], y[j], s);
+            y[i] = __ddiv_rn(s, a[i][i]);
+        }
+    }
+}
+
+// Forward substitution with the factors of lu_thread_factor<N, true, 0>:
+// apply the interchanges to y in order, then y_i -= l_ij y_j (increasing j).
+template <int N>
+__device__ __forceinline__ void lu_thread_forward(const double (&a)[N][N], const int (&piv)[N],
+                                                  double (&y)[N])
+{
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const int p = piv[k];
+#pragma unroll
+        for (int i = k + 1; i < N; ++i) {
+            const bool s = (p == i);
+            double t = y[k];
+            y[k] = sel(s, y[i], t);
+            y[i] = sel(s, t, y[i]);
+        }
+    }
+#pragma unroll
+    for (int i = 1; i < N; ++i) {
+        double s = y[i];
+#pragma unroll
+        for (int j = 0; j < i; ++j) s = __fma_rn(-a[i][j], y[j], s);
+        y[i] = s;
+    }
+}
+
+// Device-callable fused solve for one system held by the calling thread:
+// A (destroyed) x = b (overwritten by x).  Returns info; x is NaN on
+// info != 0.  This is the entry the fused Newton kernel calls.
+template <int N>
+__device__ __forceinline__ int lupp_solve(double (&a)[N][N], double (&b)[N], int (&piv)[N])
+{
+    if (any_nonfinite<N>(a)) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            piv[k] = k;
+            b[k] = nan_value();
+        }
+        return -1;
+    }
+    double rcp[N];
+    bool tiny = false;
+    double (&bb)[1][N] = *reinterpret_cast<double (*)[1][N]>(&b);
+    int info = lu_thread_factor<N, false, 1>(a, bb, piv, rcp, tiny);
+    lu_thread_backsolve<N>(a, b, rcp, tiny);
+    if (info != 0) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) b[i] = nan_value();
+    }
+    return info;
+}
+
+// ---------------------------------------------------------------------------
+// T lanes per system (row-cyclic ownership), everything in registers.
+// ---------------------------------------------------------------------------
+
+template <int N, int T>
+struct Group {
+    static constexpr int K = (N + T - 1) / T;  // row slots per lane
+    static_assert(T >= 1 && T <= 32 && (32 % T) == 0, "T must divide 32");
+    // A slot is live at step k when some lane's row in it is still below the
+    // pivot row: (T-1) + s*T > k, and the slot is not entirely phantom.
+    __host__ __device__ static constexpr bool slot_alive(int s, int k)
+    {
+        return s * T < N && (T - 1) + s * T > k;
+    }
+};
+
+// Butterfly arg-max over the T lanes of a group.  Each lane proposes
+// (value bits, row); the winner has the largest magnitude, ties to the
+// smallest row.  All lanes of the warp must call this together.
+template <int T>
+__device__ __forceinline__ void group_argmax(double &v, int &row)
+{
+#pragma unroll
+    for (int off = T / 2; off >= 1; off >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, v, off);
+        int orow = __shfl_xor_sync(0xffffffffu, row, off);
+        unsigned long long m = mag_bits(v), om = mag_bits(ov);
+        bool take = (om > m) || (om == m && orow < row);
+        v = sel(take, ov, v);
+        row = take ? orow : row;
+    }
+}
+
+// Group LUpp.  Lane t (0..T-1) of the group holds rows t + s*T in a[s][*]
+// and, for NB = 1, the matching entries of the right-hand side in b[s].
+// `lane0` is the warp lane of the group's first lane.  `active` is false for
+// groups past the end of the batch (they compute on zeros but must still
+// take part in the warp shuffles).
+// On return: pivk[s] = 0-based pivot row of step k = t + s*T (for this
+// lane's steps), rcp[s] = RN(1/u_ii) of this lane's rows, info as usual.
+template <int N, int T, bool KEEP_L, int NB>
+__device__ __forceinline__ int lu_group_factor(double (&a)[Group<N, T>::K][N],
+                                               double (&b)[Group<N, T>::K],
+                                               int (&pivk)[Group<N, T>::K],
+                                               double (&rcp)[Group<N, T>::K], int t, int lane0,
+                                               bool &tiny)
+{
+    constexpr int K = Group<N, T>::K;
+    int info = 0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const int owner_k = k % T;   // lane (in group) holding row k
+        const int slot_k = k / T;
+        // a2: local candidate, then butterfly across the group.
+        double cv = 0.0;
+        int crow = N;  // sentinel: no candidate
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            if (s * T < N && (T - 1) + s * T >= k) {
+                const int i = t + s * T;
+                const bool cand = (i >= k) && (i < N);
+                const unsigned long long m = mag_bits(a[s][k]);
+                const bool take = cand && (crow == N || m > mag_bits(cv));
+                cv = sel(take, a[s][k], cv);
+                crow = take ? i : crow;
+            }
+        }
+        group_argmax<T>(cv, crow);
+        const int p = crow;
+        const bool zero = (mag_bits(cv) == 0ULL);
+        if (t == owner_k) pivk[slot_k] = p;
+        if (zero && info == 0) info = k + 1;
+
+        // a3: interchange rows k and p between their owning lanes.
+        const int owner_p = p % T;
+        const int slot_p = p / T;
+        const int j0 = KEEP_L ? 0 : k;
+#pragma unroll
+        for (int j = j0; j < N + NB; ++j) {
+            double vk, vp = 0.0;
+            if (j < N) {
+                vk = a[slot_k][j];
+#pragma unroll
+                for (int s = 0; s < K; ++s) vp = sel(s == slot_p, a[s][j], vp);
+            } else {
+                vk = b[slot_k];
+#pragma unroll
+                for (int s = 0; s < K; ++s) vp = sel(s == slot_p, b[s], vp);
+            }
+            const double new_k = __shfl_sync(0xffffffffu, vp, lane0 + owner_p);
+            const double new_p = __shfl_sync(0xffffffffu, vk, lane0 + owner_k);
+            if (j < N) {
+#pragma unroll
+                for (int s = 0; s < K; ++s)
+                    a[s][j] = sel(t == owner_p && s == slot_p, new_p, a[s][j]);
+                if (t == owner_k) a[slot_k][j] = new_k;
+            } else {
+#pragma unroll
+                for (int s = 0; s < K; ++s) b[s] = sel(t == owner_p && s == slot_p, new_p, b[s]);
+                if (t == owner_k) b[slot_k] = new_k;
+            }
+        }
+
+        // a4: reciprocal of the pivot (the butterfly left its value in cv on
+        // every lane) and the multipliers of this lane's live rows.
+        const bool small = !zero && mag_bits(cv) < kDblMinBits;
+        const double r = __drcp_rn(cv);
+        if (t == owner_k) rcp[slot_k] = r;
+        tiny = tiny || small;
+        if (!__any_sync(0xffffffffu, small)) {
+#pragma unroll
+            for (int s = 0; s < K; ++s) {
+                if (Group<N, T>::slot_alive(s, k)) {
+                    const int i = t + s * T;
+                    const bool live = !zero && i > k && i < N;
+                    if (live) a[s][k] = __dmul_rn(a[s][k], r);
+                }
+            }
+        } else {  // some group of the warp has a pivot below DBL_MIN
+#pragma unroll
+            for (int s = 0; s < K; ++s) {
+                if (Group<N, T>::slot_alive(s, k)) {
+                    const int i = t + s * T;
+                    const bool live = !zero && i > k && i < N;
+                    if (live) a[s][k] = small ? __ddiv_rn(a[s][k], cv) : __dmul_rn(a[s][k], r);
+                }
+            }
+        }
+        // Broadcast of the pivot row u_kj (j > k) and y_k, then a5 update.
+        double uk[N + 1];
+#pragma unroll
+        for (int j = k + 1; j < N; ++j) uk[j] = __shfl_sync(0xffffffffu, a[slot_k][j], lane0 + owner_k);
+        if (NB > 0) uk[N] = __shfl_sync(0xffffffffu, b[slot_k], lane0 + owner_k);
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            if (Group<N, T>::slot_alive(s, k)) {
+                const int i = t + s * T;
+                const bool live = !zero && i > k && i < N;
+                if (live) {
+#pragma unroll
+                    for (int j = k + 1; j < N; ++j) a[s][j] = __fma_rn(-a[s][k], uk[j], a[s][j]);
+                    if (NB > 0) b[s] = __fma_rn(-a[s][k], uk[N], b[s]);
+                }
+            }
+        }
+    }
+    return info;
+}
+
+// Group back substitution for one right-hand side: lane t holds y of its rows
+// in b[s]; on return b[s] holds x of its rows.  x_i is formed by the owner of
+// row i (times RN(1/u_ii), or a division on the tiny path) and broadcast.
+template <int N, int T>
+__device__ __forceinline__ void lu_group_backsolve(const double (&a)[Group<N, T>::K][N],
+                                                   double (&b)[Group<N, T>::K],
+                                                   const double (&rcp)[Group<N, T>::K], int t,
+                                                   int lane0, bool tiny)
+{
+    constexpr int K = Group<N, T>::K;
+    const bool any_tiny = __any_sync(0xffffffffu, tiny);
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {
+        const int owner = i % T;
+        const int slot = i / T;
+        double xi;
+        if (!any_tiny) {
+            xi = __dmul_rn(b[slot], rcp[slot]);
+        } else {
+            xi = tiny ? __ddiv_rn(b[slot], a[slot][i]) : __dmul_rn(b[slot], rcp[slot]);
+        }
+        xi = __shfl_sync(0xffffffffu, xi, lane0 + owner);
+        if (t == owner) b[slot] = xi;
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            if (s * T < i) {  // some lane of this slot has a row below i
+                const int r = t + s * T;
+                if (r < i) b[s] = __fma_rn(-a[s][i], xi, b[s]);
+            }
+        }
+    }
+}
+
+}  // namespace dev
+}  // namespace tl

@@ -1,0 +1,52 @@
+// tl_handle.h -- the opaque tl_handle of the C ABI (library-internal).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <functional>
+#include <unordered_map>
+#include <utility>
+
+#include "tinylu.h"
+#include "tl_internal.h"
+
+namespace tl {
+
+// Dispatch choice for one (n, layout, op): lanes per system (0 = default
+// policy) and block size (0 = occupancy + wave-fill heuristic per launch).
+struct Choice {
+    int lanes;
+    int block;
+};
+
+struct PairHash {
+    size_t operator()(const std::pair<const void *, int> &p) const
+    {
+        return std::hash<const void *>()(p.first) ^ (static_cast<size_t>(p.second) * 0x9e3779b97f4a7c15ULL);
+    }
+};
+
+int default_lanes(int n);
+const Variant *find_variant(int n, int layout, int op, int lanes);
+tl_status fail_arg(tl_handle *h, int pos);
+tl_status fail_cuda(tl_handle *h, cudaError_t e);
+int pick_block(tl_handle *h, const void *kernel, int64_t threads);
+tl_status launch_variant(tl_handle *h, const Variant *v, int block, SolveArgs &args, cudaStream_t stream);
+tl_status launch_op(tl_handle *h, int n, int layout, int op, SolveArgs &args, cudaStream_t stream);
+
+}  // namespace tl
+
+struct tl_handle {
+    int device = 0;
+    int sm_count = 1;
+    int max_threads_per_sm = 2048;
+    int last_cuda_error = 0;
+    int last_bad_arg = 0;
+    tl::Choice choice[TL_MAX_N + 1][2][tl::kOps] = {};
+    std::unordered_map<std::pair<const void *, int>, int, tl::PairHash> occupancy;
+    // device workspace owned by the handle (grown on demand, never inside a
+    // stream capture) and pinned host staging buffers
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    void *host_stage[2] = {nullptr, nullptr};
+    size_t host_stage_bytes = 0;
+};

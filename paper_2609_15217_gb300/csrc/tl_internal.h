@@ -1,0 +1,47 @@
+// tl_internal.h -- types shared by the kernel instantiations and the C ABI
+// implementation (not part of the public interface).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tl {
+
+enum : int { kPerSystem = 0, kInterleaved = 1 };
+enum : int { kGesv = 0, kGetrf = 1, kGetrs = 2 };
+
+// Arguments of every batched solve kernel.  Unused pointers are null.
+//   gesv : A, b in; x, ipiv, info out; LU out when factors are requested
+//   getrf: LU in/out (A is ignored); ipiv, info out
+//   getrs: A = factors in, ipiv in, x = right-hand sides in / solutions out
+struct SolveArgs {
+    const double *A;
+    double *LU;
+    const double *b;
+    double *x;
+    int32_t *ipiv;
+    int32_t *info;
+    int64_t ld;
+    int64_t batch;
+    int nrhs;
+};
+
+// Kernel variant for one (n, layout, operation): how many lanes share a
+// system (1 = one thread per system) and the launch entry.
+struct Variant {
+    int lanes;                     // T
+    const void *kernel;            // __global__ function, for occupancy queries
+    int regs_hint;                 // 0 when unknown
+};
+
+// Registry filled by the instantiation units (tl_inst.cu, one per (N, T)).
+enum : int { kOpGesv = 0, kOpGesvLU = 1, kOpGetrf = 2, kOpGetrs = 3 };
+constexpr int kOps = 4;
+constexpr int kMaxVariants = 6;
+struct VariantList {
+    int count;
+    Variant v[kMaxVariants];
+};
+VariantList &registry(int n, int layout, int op);
+void register_variant(int n, int layout, int op, int lanes, const void *kernel);
+
+}  // namespace tl

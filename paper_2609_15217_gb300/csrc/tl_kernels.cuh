@@ -1,0 +1,279 @@
+// tl_kernels.cuh -- batched LUpp kernels (gesv / getrf / getrs) built on the
+// device-callable solvers of tl_device.cuh, for the two storage layouts of
+// the C ABI.  Instantiated per system size N in tl_inst_*.cu.
+#pragma once
+#include "tl_device.cuh"
+#include "tl_internal.h"
+
+namespace tl {
+
+// Element offsets in the two layouts (include/tinylu.h).
+template <int N, int LAYOUT>
+struct Idx {
+    __device__ __forceinline__ static int64_t a(int64_t s, int i, int j, int64_t ld)
+    {
+        return LAYOUT == kInterleaved ? static_cast<int64_t>(j * N + i) * ld + s
+                                      : s * (N * N) + (j * N + i);
+    }
+    __device__ __forceinline__ static int64_t v(int64_t s, int i, int64_t ld)
+    {
+        return LAYOUT == kInterleaved ? static_cast<int64_t>(i) * ld + s : s * N + i;
+    }
+    // right-hand side r of a multi-RHS block
+    __device__ __forceinline__ static int64_t rhs(int64_t s, int i, int r, int nrhs, int64_t ld)
+    {
+        return LAYOUT == kInterleaved ? static_cast<int64_t>(r * N + i) * ld + s
+                                      : s * (static_cast<int64_t>(N) * nrhs) + (r * N + i);
+    }
+};
+
+// Streaming loads/stores: every input is read once and every output written
+// once, so keep them out of the way of the L2 lines that are reused.
+__device__ __forceinline__ double ld_stream(const double *p) { return __ldcs(p); }
+__device__ __forceinline__ void st_stream(double *p, double v) { __stcs(p, v); }
+__device__ __forceinline__ void st_stream(int32_t *p, int32_t v) { __stcs(p, v); }
+
+// ---------------------------------------------------------------------------
+// One thread per system.
+// MODE: kGesv (A const, LU_out optional via KEEP), kGetrf (A in place).
+// ---------------------------------------------------------------------------
+template <int N, int LAYOUT, int MODE, bool KEEP>
+__global__ void __launch_bounds__(128) k_factor_thread(SolveArgs args)
+{
+    const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (s >= args.batch) return;
+    using I = Idx<N, LAYOUT>;
+    const double *A = (MODE == kGetrf) ? args.LU : args.A;
+    double a[N][N];
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+#pragma unroll
+        for (int i = 0; i < N; ++i) a[i][j] = (MODE == kGetrf) ? A[I::a(s, i, j, args.ld)]
+                                                                 : ld_stream(A + I::a(s, i, j, args.ld));
+    double b[1][N];
+    if (MODE == kGesv) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) b[0][i] = ld_stream(args.b + I::v(s, i, args.ld));
+    }
+    const bool bad = dev::any_nonfinite<N>(a);
+    int piv[N];
+    double rcp[N];
+    bool tiny = false;
+    int info = dev::lu_thread_factor<N, KEEP, (MODE == kGesv) ? 1 : 0>(a, b, piv, rcp, tiny);
+    if (MODE == kGesv) dev::lu_thread_backsolve<N>(a, b[0], rcp, tiny);
+    if (bad) info = -1;
+
+    if (MODE == kGesv) {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            st_stream(args.x + I::v(s, i, args.ld), info != 0 ? dev::nan_value() : b[0][i]);
+    }
+    if (KEEP) {
+        // info = -1: nothing is factored; the factors output keeps A.
+        double *LU = args.LU;
+        if (!bad) {
+#pragma unroll
+            for (int j = 0; j < N; ++j)
+#pragma unroll
+                for (int i = 0; i < N; ++i) st_stream(LU + I::a(s, i, j, args.ld), a[i][j]);
+        } else if (MODE == kGesv) {
+            for (int j = 0; j < N; ++j)
+                for (int i = 0; i < N; ++i) LU[I::a(s, i, j, args.ld)] = args.A[I::a(s, i, j, args.ld)];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < N; ++k) st_stream(args.ipiv + I::v(s, k, args.ld), bad ? k + 1 : piv[k] + 1);
+    st_stream(args.info + s, info);
+}
+
+// One thread per system: solve with given factors, nrhs right-hand sides.
+template <int N, int LAYOUT>
+__global__ void __launch_bounds__(128) k_getrs_thread(SolveArgs args)
+{
+    const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (s >= args.batch) return;
+    using I = Idx<N, LAYOUT>;
+    double a[N][N];
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+#pragma unroll
+        for (int i = 0; i < N; ++i) a[i][j] = args.A[I::a(s, i, j, args.ld)];
+    int piv[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) piv[k] = args.ipiv[I::v(s, k, args.ld)] - 1;
+    double rcp[N];
+    unsigned long long smallest = ~0ULL;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        rcp[i] = __drcp_rn(a[i][i]);
+        unsigned long long m = dev::mag_bits(a[i][i]);
+        smallest = m < smallest ? m : smallest;
+    }
+    const bool tiny = smallest < dev::kDblMinBits;
+    for (int r = 0; r < args.nrhs; ++r) {
+        double y[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) y[i] = args.x[I::rhs(s, i, r, args.nrhs, args.ld)];
+        dev::lu_thread_forward<N>(a, piv, y);
+        dev::lu_thread_backsolve<N>(a, y, rcp, tiny);
+#pragma unroll
+        for (int i = 0; i < N; ++i) args.x[I::rhs(s, i, r, args.nrhs, args.ld)] = y[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// T lanes per system (row-cyclic).  Whole warps stay resident until the end
+// because every lane takes part in the shuffles; lanes of groups past the
+// batch end compute on zeros and store nothing.
+// ---------------------------------------------------------------------------
+
+// OR of a predicate over the T lanes of a group.
+template <int T>
+__device__ __forceinline__ bool group_any(bool v)
+{
+    int x = v ? 1 : 0;
+#pragma unroll
+    for (int off = T / 2; off >= 1; off >>= 1) x |= __shfl_xor_sync(0xffffffffu, x, off);
+    return x != 0;
+}
+
+template <int N, int T, int LAYOUT, int MODE, bool KEEP>
+__global__ void __launch_bounds__(128) k_factor_group(SolveArgs args)
+{
+    constexpr int K = dev::Group<N, T>::K;
+    const int lane = threadIdx.x & 31;
+    const int t = lane % T;
+    const int lane0 = lane - t;
+    const int64_t s = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / T;
+    const int64_t warp_first = ((static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) & ~31LL) / T;
+    if (warp_first >= args.batch) return;  // the whole warp is past the end
+    const bool active = s < args.batch;
+    using I = Idx<N, LAYOUT>;
+    const double *A = (MODE == kGetrf) ? args.LU : args.A;
+
+    double a[K][N];
+    double b[K];
+#pragma unroll
+    for (int sl = 0; sl < K; ++sl) {
+        const int i = t + sl * T;
+        const bool ok = active && i < N;
+#pragma unroll
+        for (int j = 0; j < N; ++j) a[sl][j] = ok ? A[I::a(s, i, j, args.ld)] : 0.0;
+        b[sl] = (MODE == kGesv && ok) ? ld_stream(args.b + I::v(s, i, args.ld)) : 0.0;
+    }
+    bool mybad = false;
+#pragma unroll
+    for (int sl = 0; sl < K; ++sl)
+#pragma unroll
+        for (int j = 0; j < N; ++j) mybad |= dev::is_nonfinite(a[sl][j]);
+    const bool bad = group_any<T>(mybad);
+
+    int pivk[K];
+    double rcp[K];
+    bool tiny = false;
+    int info = dev::lu_group_factor<N, T, KEEP, (MODE == kGesv) ? 1 : 0>(a, b, pivk, rcp, t, lane0, tiny);
+    if (MODE == kGesv) dev::lu_group_backsolve<N, T>(a, b, rcp, t, lane0, tiny);
+    if (bad) info = -1;
+    if (!active) return;
+
+#pragma unroll
+    for (int sl = 0; sl < K; ++sl) {
+        const int i = t + sl * T;
+        if (i < N) {
+            if (MODE == kGesv) st_stream(args.x + I::v(s, i, args.ld), info != 0 ? dev::nan_value() : b[sl]);
+            st_stream(args.ipiv + I::v(s, i, args.ld), bad ? i + 1 : pivk[sl] + 1);
+            if (KEEP && !bad) {
+#pragma unroll
+                for (int j = 0; j < N; ++j) st_stream(args.LU + I::a(s, i, j, args.ld), a[sl][j]);
+            } else if (KEEP && MODE == kGesv) {
+                for (int j = 0; j < N; ++j) args.LU[I::a(s, i, j, args.ld)] = args.A[I::a(s, i, j, args.ld)];
+            }
+        }
+    }
+    if (t == 0) st_stream(args.info + s, info);
+}
+
+// T lanes per system: solve with given factors, nrhs right-hand sides.
+template <int N, int T, int LAYOUT>
+__global__ void __launch_bounds__(128) k_getrs_group(SolveArgs args)
+{
+    constexpr int K = dev::Group<N, T>::K;
+    const int lane = threadIdx.x & 31;
+    const int t = lane % T;
+    const int lane0 = lane - t;
+    const int64_t s = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / T;
+    const int64_t warp_first = ((static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) & ~31LL) / T;
+    if (warp_first >= args.batch) return;
+    const bool active = s < args.batch;
+    using I = Idx<N, LAYOUT>;
+
+    double a[K][N];
+    int pivk[K];
+    double rcp[K];
+    bool tiny = false;
+#pragma unroll
+    for (int sl = 0; sl < K; ++sl) {
+        const int i = t + sl * T;
+        const bool ok = active && i < N;
+#pragma unroll
+        for (int j = 0; j < N; ++j) a[sl][j] = ok ? args.A[I::a(s, i, j, args.ld)] : 0.0;
+        pivk[sl] = ok ? args.ipiv[I::v(s, i, args.ld)] - 1 : i;
+    }
+    // The diagonal entry of row i sits in column i, a run-time index here;
+    // re-read it with a select chain so the register array stays static.
+#pragma unroll
+    for (int sl = 0; sl < K; ++sl) {
+        const int i = t + sl * T;
+        double d = 0.0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) d = dev::sel(j == i, a[sl][j], d);
+        const bool ok = active && i < N;
+        rcp[sl] = __drcp_rn(d);
+        tiny = tiny || (ok && dev::mag_bits(d) < dev::kDblMinBits);
+    }
+    for (int r = 0; r < args.nrhs; ++r) {
+        double y[K];
+#pragma unroll
+        for (int sl = 0; sl < K; ++sl) {
+            const int i = t + sl * T;
+            y[sl] = (active && i < N) ? args.x[I::rhs(s, i, r, args.nrhs, args.ld)] : 0.0;
+        }
+        // interchanges in order k = 0..N-1 (pivot of step k broadcast by its owner)
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const int owner_k = k % T, slot_k = k / T;
+            const int p = __shfl_sync(0xffffffffu, pivk[slot_k], lane0 + owner_k);
+            const int owner_p = p % T, slot_p = p / T;
+            double vp = 0.0;
+#pragma unroll
+            for (int sl = 0; sl < K; ++sl) vp = dev::sel(sl == slot_p, y[sl], vp);
+            const double new_k = __shfl_sync(0xffffffffu, vp, lane0 + owner_p);
+            const double new_p = __shfl_sync(0xffffffffu, y[slot_k], lane0 + owner_k);
+#pragma unroll
+            for (int sl = 0; sl < K; ++sl) y[sl] = dev::sel(t == owner_p && sl == slot_p, new_p, y[sl]);
+            if (t == owner_k) y[slot_k] = new_k;
+        }
+        // forward: y_i -= l_ik y_k for i > k, k increasing
+#pragma unroll
+        for (int k = 0; k < N - 1; ++k) {
+            const double yk = __shfl_sync(0xffffffffu, y[k / T], lane0 + k % T);
+#pragma unroll
+            for (int sl = 0; sl < K; ++sl) {
+                if (dev::Group<N, T>::slot_alive(sl, k)) {
+                    const int i = t + sl * T;
+                    if (i > k && i < N) y[sl] = __fma_rn(-a[sl][k], yk, y[sl]);
+                }
+            }
+        }
+        dev::lu_group_backsolve<N, T>(a, y, rcp, t, lane0, tiny);
+        if (active) {
+#pragma unroll
+            for (int sl = 0; sl < K; ++sl) {
+                const int i = t + sl * T;
+                if (i < N) args.x[I::rhs(s, i, r, args.nrhs, args.ld)] = y[sl];
+            }
+        }
+    }
+}
+
+}  // namespace tl

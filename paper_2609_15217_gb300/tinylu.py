@@ -1,0 +1,167 @@
+"""ctypes binding of the C ABI in include/tinylu.h (argument marshalling only).
+
+Every function has the C name and argument order; tensor arguments may be
+torch tensors (their data_ptr() is passed), raw integer addresses, or None
+for a NULL pointer.  `stream` defaults to torch's current CUDA stream.  Every
+step of the computation runs in libtinylu.so: importing this module raises
+if the library has not been built -- there is no fallback.
+"""
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtinylu.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+        "(the CUDA library is the only compute path)")
+
+_lib = C.CDLL(LIB_PATH)
+
+TL_OK, TL_ERR_INVALID_ARG, TL_ERR_CUDA, TL_ERR_NO_MEMORY, TL_ERR_UNSUPPORTED, TL_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+TL_LAYOUT_PER_SYSTEM, TL_LAYOUT_INTERLEAVED = 0, 1
+TL_PREC_FP64, TL_PREC_FP32_IR = 0, 1
+TL_LAW_NORTON, TL_LAW_TANH = 0, 1
+TL_NEWTON_CONVERGED, TL_NEWTON_MAX_ITER, TL_NEWTON_SINGULAR, TL_NEWTON_NONFINITE = 0, 1, 2, 3
+TL_MAX_N = 32
+
+
+class tl_law(C.Structure):
+    _fields_ = [("id", C.c_int32), ("n", C.c_int32), ("params", C.c_double * 6)]
+
+
+_vp = C.c_void_p
+_i64 = C.c_int64
+_int = C.c_int
+
+_SIGS = {
+    "tl_create": ([C.POINTER(_vp)], _int),
+    "tl_destroy": ([_vp], _int),
+    "tl_status_string": ([_int], C.c_char_p),
+    "tl_last_cuda_error": ([_vp, C.POINTER(_int)], _int),
+    "tl_last_bad_arg": ([_vp], _int),
+    "tl_getrf_batched": ([_vp, _int, _vp, _int, _i64, _vp, _vp, _i64, _vp], _int),
+    "tl_getrs_batched": ([_vp, _int, _int, _vp, _vp, _int, _i64, _vp, _i64, _vp], _int),
+    "tl_gesv_batched": ([_vp, _int, _vp, _vp, _vp, _vp, _vp, _vp, _int, _i64, _i64, _vp], _int),
+    "tl_lupp_solve_batched": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _int, _vp, _vp], _int),
+    "tl_newton_integrate": ([_vp, C.POINTER(tl_law), _i64, _vp, _vp, _vp, _vp, _vp, C.c_double, _int, _vp], _int),
+    "tl_autotune": ([_vp, _int, _int, _int, C.c_char_p], _int),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+def _p(x):
+    """Pointer of a tensor / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+class TinyLUError(RuntimeError):
+    def __init__(self, fn, status, detail=""):
+        msg = _lib.tl_status_string(status).decode()
+        super().__init__(f"{fn}: {msg}{detail}")
+        self.status = status
+
+
+def check(fn, status, h=None):
+    if status == TL_OK:
+        return status
+    detail = ""
+    if h is not None:
+        if status == TL_ERR_INVALID_ARG:
+            detail = f" (argument {tl_last_bad_arg(h)})"
+        elif status == TL_ERR_CUDA:
+            e = C.c_int(0)
+            _lib.tl_last_cuda_error(h, C.byref(e))
+            detail = f" (cudaError {e.value})"
+    raise TinyLUError(fn, status, detail)
+
+
+# ---------------------------------------------------------------------------
+# C ABI entry points (same names)
+# ---------------------------------------------------------------------------
+
+def tl_create():
+    h = _vp()
+    check("tl_create", _lib.tl_create(C.byref(h)))
+    return h
+
+
+def tl_destroy(h):
+    return _lib.tl_destroy(h)
+
+
+def tl_status_string(status):
+    return _lib.tl_status_string(status).decode()
+
+
+def tl_last_cuda_error(h):
+    e = C.c_int(0)
+    _lib.tl_last_cuda_error(h, C.byref(e))
+    return e.value
+
+
+def tl_last_bad_arg(h):
+    return _lib.tl_last_bad_arg(h)
+
+
+def tl_getrf_batched(h, n, A, layout, ld_batch, ipiv, info, batch, stream=None):
+    return _lib.tl_getrf_batched(h, n, _p(A), layout, ld_batch, _p(ipiv), _p(info), batch, _stream(stream))
+
+
+def tl_getrs_batched(h, n, nrhs, LU, ipiv, layout, ld_batch, B, batch, stream=None):
+    return _lib.tl_getrs_batched(h, n, nrhs, _p(LU), _p(ipiv), layout, ld_batch, _p(B), batch, _stream(stream))
+
+
+def tl_gesv_batched(h, n, A, LU_out, b, x, ipiv, info, layout, ld_batch, batch, stream=None):
+    return _lib.tl_gesv_batched(h, n, _p(A), _p(LU_out), _p(b), _p(x), _p(ipiv), _p(info), layout, ld_batch,
+                                batch, _stream(stream))
+
+
+def tl_lupp_solve_batched(h, batch, n, a_off, A, b_off, b, x, piv_off, ipiv, info, prec=TL_PREC_FP64,
+                          refine_steps=None, stream=None):
+    return _lib.tl_lupp_solve_batched(h, batch, _p(n), _p(a_off), _p(A), _p(b_off), _p(b), _p(x), _p(piv_off),
+                                      _p(ipiv), _p(info), prec, _p(refine_steps), _stream(stream))
+
+
+def make_law(law_id, n, params=()):
+    law = tl_law()
+    law.id = law_id
+    law.n = n
+    for i, v in enumerate(params):
+        law.params[i] = float(v)
+    return law
+
+
+def tl_newton_integrate(h, law, npoints, inputs, x, outputs, iterations, status, rtol, max_iter, stream=None):
+    return _lib.tl_newton_integrate(h, C.byref(law), npoints, _p(inputs), _p(x), _p(outputs), _p(iterations),
+                                    _p(status), rtol, max_iter, _stream(stream))
+
+
+def tl_autotune(h, n_min, n_max, layout, table_path=None):
+    return _lib.tl_autotune(h, n_min, n_max, layout, table_path.encode() if table_path else None)
+
+
+def library():
+    """The loaded ctypes library (for symbol checks)."""
+    return _lib
