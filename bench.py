@@ -1,0 +1,447 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched FP64 LUpp hot path on GB300.
+
+One step = the standalone FP64 sweep (every n in 1..32, 2^20 systems per n
+capped at 6 GiB of A, b, x, ipiv and info per n; half U[-1,1] entries, half
+A = U diag(s) V^T with kappa log-uniform in [1e2, 1e8]; b = A x_true), all
+systems resident in HBM in the interleaved batch-minor layout, solved by
+tl_gesv_batched.  The per-system layout sweep is timed the same way and
+reported beside it; when the fused Newton kernel is available the Norton
+integration over 2^22 points is timed too.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead (the reference arm).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "FP64 tiny-LUpp solves/s vs n; Newton points/s; p50/p99 request latency"
+UNIT = "solves/s"
+CAP_BYTES = 6 * (1 << 30)
+SWEEP_BATCH = 1 << 20
+NEWTON_POINTS = 1 << 22
+
+
+_T0 = time.perf_counter()
+
+
+def log(msg):
+    sys.stderr.write(f"[bench {time.perf_counter() - _T0:8.1f}s] {msg}\n")
+    sys.stderr.flush()
+
+
+def sweep_batch(n, full=SWEEP_BATCH):
+    """2^20 systems, capped so A, b, x, ipiv and info fit in 6 GiB."""
+    per = 8 * n * n + 16 * n + 4 * n + 4
+    return min(full, CAP_BYTES // per)
+
+
+def flops_per_system(n):
+    """Algorithmic FP64 flops of one fused getrf + getrs (FMA = 2 flops):
+    getrf (n-1)n(2n-1)/6 FMAs, n(n-1)/2 multipliers, n-1 reciprocals;
+    getrs n(n-1) FMAs and n divisions."""
+    fma = (n - 1) * n * (2 * n - 1) // 6 + n * (n - 1)
+    return 2 * fma + n * (n - 1) // 2 + (n - 1) + n
+
+
+def bytes_per_system(n):
+    """A and b read, x, ipiv (int32) and info (int32) written."""
+    return 8 * n * n + 8 * n + 8 * n + 4 * n + 4
+
+
+# FP64 pipe of the GB300: 152 SMs x 4 sub-partitions x 0.5 DFMA lane/clock
+# (measured: one warp-wide DFMA per 64 clocks per sub-partition) x 2 flops x
+# 2.07 GHz maximum SM clock.
+FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class Clocks:
+    """Samples SM clock and throttle reasons with nvidia-smi during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        top = max(sm)
+        loaded = [v for v in sm if v >= 0.5 * top] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def make_sweep(n_list, layout, seed_base, device, torch, L, I):
+    """Generate every n's batch on the device and pack it in `layout`."""
+    data = {}
+    for n in n_list:
+        S = sweep_batch(n)
+        log(f"generate n={n} batch={S} layout={layout}")
+        A, b, _x = I.sweep_systems_torch(n, S, seed_base * 1000 + n, device)
+        ld = L.pad_ld(S)
+        dA = L.matrices_to_layout(A, layout, ld)
+        db = L.vectors_to_layout(b, layout, ld)
+        del A, b, _x
+        rows = n * (ld if layout == 1 else S)
+        data[n] = dict(S=S, ld=ld, A=dA, b=db, x=torch.empty(rows, dtype=torch.float64, device=device),
+                       ipiv=torch.empty(rows, dtype=torch.int32, device=device),
+                       info=torch.empty(S, dtype=torch.int32, device=device))
+    torch.cuda.synchronize()
+    return data
+
+
+def run_sweep(tl, h, data, layout, stream, torch, events=None):
+    for n, d in data.items():
+        if events is not None:
+            events[n][0].record(stream)
+        st = tl.tl_gesv_batched(h, n, d["A"], None, d["b"], d["x"], d["ipiv"], d["info"], layout, d["ld"],
+                                d["S"], stream.cuda_stream)
+        if st != 0:
+            tl.check("tl_gesv_batched", st, h)
+        if events is not None:
+            events[n][1].record(stream)
+
+
+def time_sweep(tl, h, data, layout, steps, warmup, torch, dist_barrier):
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        run_sweep(tl, h, data, layout, stream, torch)
+    torch.cuda.synchronize()
+    per_n = {n: [] for n in data}
+    dist_barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    ev = {n: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for n in data}
+    step_ms = []
+    for _ in range(steps):
+        t0.record(stream)
+        run_sweep(tl, h, data, layout, stream, torch, ev)
+        t1.record(stream)
+        t1.synchronize()
+        step_ms.append(t0.elapsed_time(t1))
+        for n in data:
+            per_n[n].append(ev[n][0].elapsed_time(ev[n][1]))
+    torch.cuda.synchronize()
+    dist_barrier()
+    return step_ms, per_n
+
+
+def sweep_e2e(tl, h, n_list, layout, steps, warmup, torch, device, L):
+    """Same sweep through host buffers: every step copies each n's A and b
+    from pinned host memory, solves, and copies x, ipiv and info back.  One
+    pinned pool (sized for the largest n, U[-1,1] entries) backs every n."""
+    sizes = {}
+    h2d = d2h = 0
+    for n in n_list:
+        S = sweep_batch(n)
+        ld = L.pad_ld(S)
+        rows = n * (ld if layout == 1 else S)
+        sizes[n] = (S, ld, n * rows, rows)
+        h2d += (n * rows + rows) * 8
+        d2h += rows * 8 + rows * 4 + S * 4
+    bigA = max(v[2] for v in sizes.values())
+    bigv = max(v[3] for v in sizes.values())
+    bigS = max(v[0] for v in sizes.values())
+    g = torch.Generator()
+    g.manual_seed(9001)
+    hA = torch.empty(bigA, dtype=torch.float64).uniform_(-1.0, 1.0, generator=g).pin_memory()
+    hb = torch.empty(bigv, dtype=torch.float64).uniform_(-1.0, 1.0, generator=g).pin_memory()
+    hx = torch.empty(bigv, dtype=torch.float64).pin_memory()
+    hp = torch.empty(bigv, dtype=torch.int32).pin_memory()
+    hi = torch.empty(bigS, dtype=torch.int32).pin_memory()
+    dA = torch.empty(bigA, dtype=torch.float64, device=device)
+    db = torch.empty(bigv, dtype=torch.float64, device=device)
+    dx = torch.empty(bigv, dtype=torch.float64, device=device)
+    dp = torch.empty(bigv, dtype=torch.int32, device=device)
+    di = torch.empty(bigS, dtype=torch.int32, device=device)
+    stream = torch.cuda.current_stream()
+
+    def one_step():
+        for n in n_list:
+            S, ld, na, nv = sizes[n]
+            dA[:na].copy_(hA[:na], non_blocking=True)
+            db[:nv].copy_(hb[:nv], non_blocking=True)
+            st = tl.tl_gesv_batched(h, n, dA, None, db, dx, dp, di, layout, ld, S, stream.cuda_stream)
+            if st != 0:
+                tl.check("tl_gesv_batched", st, h)
+            hx[:nv].copy_(dx[:nv], non_blocking=True)
+            hp[:nv].copy_(dp[:nv], non_blocking=True)
+            hi[:S].copy_(di[:S], non_blocking=True)
+
+    for _ in range(warmup):
+        one_step()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(steps):
+        t0.record(stream)
+        one_step()
+        t1.record(stream)
+        t1.synchronize()
+        ms.append(t0.elapsed_time(t1))
+    total = sum(v[0] for v in sizes.values())
+    med = statistics.median(ms)
+    return {"value": total / (med / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": med,
+            "inputs": "one pinned host pool of U[-1,1] entries (sized for the largest n) backs every n's A and b"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sweep_rate(n_list, target_s=0.3, samples=None, seed_base=1236, max_sample=1 << 15):
+    """Time the oracle on a bounded sample of each n's batch and extrapolate
+    to the full sweep.  Returns (solves/s over the sweep, threads, sample)."""
+    import oracle
+    from paper_2609_15217_gb300 import inputs as I
+    threads = oracle.max_threads()
+    total_S = 0
+    total_t = 0.0
+    sample = {}
+    for n in n_list:
+        m = samples[n] if samples else 256
+        A, b, _, _ = I.sweep_systems(n, m, seed_base * 1000 + n)
+        t = time.perf_counter()
+        oracle.gesv(A, b)
+        dt = time.perf_counter() - t
+        if not samples:
+            m2 = int(min(sweep_batch(n), max_sample, max(256, m * target_s / max(dt, 1e-6))))
+            A, b, _, _ = I.sweep_systems(n, m2, seed_base * 1000 + n)
+            t = time.perf_counter()
+            oracle.gesv(A, b)
+            dt = time.perf_counter() - t
+            m = m2
+        sample[n] = m
+        S = sweep_batch(n)
+        total_S += S
+        total_t += S * dt / m
+    return total_S / total_t, threads, sample
+
+
+def reference_arm(args):
+    """--impl reference: the CPU oracle (as it stands) on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_list = list(range(args.nmin, args.nmax + 1))
+    vals = []
+    sample = None
+    t_all = time.perf_counter()
+    for i in range(args.warmup + args.steps):
+        v, threads, sample = oracle_sweep_rate(n_list, target_s=args.ref_seconds_per_n, samples=sample)
+        if i >= args.warmup:
+            vals.append(v)
+    v = statistics.median(vals)
+    sample_desc = ("oracle gesv on the first m_n systems of each n's sweep batch (m_n per n: "
+                   + ", ".join(f"{n}:{m}" for n, m in sample.items())
+                   + "), time extrapolated linearly to the full per-n batch sizes")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "standalone FP64 sweep n=1..32, 2^20 systems per n (6 GiB cap), interleaved",
+                   "L2": "n/a (host)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample_desc},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": time.perf_counter() - t_all,
+    }
+    print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nmin", type=int, default=1)
+    ap.add_argument("--nmax", type=int, default=32)
+    ap.add_argument("--no-per-system", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-seconds-per-n", type=float, default=0.3)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    from paper_2609_15217_gb300 import inputs as I
+    from paper_2609_15217_gb300 import layout as L
+    from paper_2609_15217_gb300 import tinylu as tl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    h = tl.tl_create()
+    n_list = list(range(args.nmin, args.nmax + 1))
+    t_gen = time.perf_counter()
+    data = make_sweep(n_list, 1, 1236 + 100 * rank, device, torch, L, I)
+    gen_s = time.perf_counter() - t_gen
+
+    log("timing interleaved sweep")
+    with Clocks(local) as clk:
+        step_ms, per_n = time_sweep(tl, h, data, 1, args.steps, args.warmup, torch, barrier)
+    clocks = clk.summary()
+
+    med_step = statistics.median(step_ms)
+    if dist is not None:
+        t = torch.tensor([med_step], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        med_step = float(t.item())
+    systems_rank = sum(d["S"] for d in data.values())
+    value = systems_rank * world / (med_step / 1e3)
+
+    per_n_out = {}
+    flops_total = 0.0
+    for n, d in data.items():
+        ms = statistics.median(per_n[n])
+        f = flops_per_system(n) * d["S"]
+        flops_total += f
+        per_n_out[n] = {"batch": d["S"], "ms": round(ms, 4), "solves_per_s": d["S"] / (ms / 1e3),
+                        "fp64_tflops": f / (ms / 1e3) / 1e12,
+                        "fp64_frac": f / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                        "gbs": bytes_per_system(n) * d["S"] / (ms / 1e3) / 1e9}
+    dom = max(per_n_out, key=lambda n: per_n_out[n]["ms"])
+    dom_flops = flops_per_system(dom) * data[dom]["S"]
+    achieved = dom_flops / (per_n_out[dom]["ms"] / 1e3) / 1e12
+    roofline = {"bound": "alu", "pipe": "fp64", "kernel": f"gesv n={dom} interleaved",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 4 SMSPs x 0.5 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25)",
+                "sweep_fp64_frac": flops_total / (med_step / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
+    del data
+    torch.cuda.empty_cache()
+
+    extra = {}
+    if not args.no_per_system:
+        log("per-system layout sweep")
+        data_ps = make_sweep(n_list, 0, 1236 + 100 * rank, device, torch, L, I)
+        ms_ps, per_n_ps = time_sweep(tl, h, data_ps, 0, max(2, args.steps // 2), 1, torch, barrier)
+        sys_ps = sum(d["S"] for d in data_ps.values())
+        extra["per_system_layout"] = {
+            "value": sys_ps * world / (statistics.median(ms_ps) / 1e3), "unit": UNIT,
+            "ms_per_step": statistics.median(ms_ps),
+            "per_n_solves_per_s": {n: data_ps[n]["S"] / (statistics.median(per_n_ps[n]) / 1e3) for n in data_ps}}
+        del data_ps
+        torch.cuda.empty_cache()
+
+    e2e = None
+    if not args.no_e2e:
+        log("end-to-end sweep")
+        e2e = sweep_e2e(tl, h, n_list, 1, max(2, args.steps // 2), 1, torch, device, L)
+        e2e["value"] *= world
+        torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        log("cpu baseline")
+        v, threads, sample = oracle_sweep_rate(n_list)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "oracle gesv (OpenMP over systems) on the first m_n systems of each n's sweep batch "
+                         f"({sum(sample.values())} systems in total, ~0.3 s per n), extrapolated to the full "
+                         "per-n batch sizes"}
+
+    log("done")
+    tl.tl_destroy(h)
+    launches = len(n_list) * args.steps
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": med_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "standalone FP64 sweep: n=1..32, 2^20 systems per n capped at 6 GiB "
+                                   "(n>=27), half U[-1,1], half kappa in [1e2,1e8], b=A x_true; interleaved "
+                                   "batch-minor layout, tl_gesv_batched",
+                       "systems_per_step": systems_rank, "L2": "inputs larger than L2 (each step streams "
+                       f"{sum(bytes_per_system(n) * sweep_batch(n) for n in n_list) / 1e9:.1f} GB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks, "per_n": per_n_out, "gen_s": gen_s, **extra,
+        }
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

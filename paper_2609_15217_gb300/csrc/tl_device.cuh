@@ -38,14 +38,38 @@ constexpr unsigned long long kMagMask = 0x7fffffffffffffffULL;
 constexpr unsigned long long kDblMinBits = 0x0010000000000000ULL;  // DBL_MIN
 constexpr unsigned long long kInfBits = 0x7ff0000000000000ULL;      // +Inf
 
+// |v| as its IEEE bit pattern (an unsigned integer that orders like |v| for
+// every non-NaN value).  Written as inline PTX on the high word: in plain C++
+// the compiler recognizes the mask as fabs() and issues it on the FP64 pipe,
+// which costs as much as an FMA on this GPU.
 __device__ __forceinline__ unsigned long long mag_bits(double v)
 {
-    return static_cast<unsigned long long>(__double_as_longlong(v)) & kMagMask;
+    unsigned long long r;
+    asm("{\n\t.reg .b32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\tand.b32 hi, hi, 0x7fffffff;\n\t"
+        "mov.b64 %0, {lo, hi};\n\t}"
+        : "=l"(r)
+        : "d"(v));
+    return r;
 }
 
 __device__ __forceinline__ bool is_nonfinite(double v) { return mag_bits(v) >= kInfBits; }
 
 __device__ __forceinline__ double nan_value() { return __longlong_as_double(0x7ff8000000000000LL); }
+
+// -x by flipping the sign bit on the integer pipe.  The FP64 pipe is the
+// scarce unit on this GPU (one warp-wide DFMA per 64 clocks per SM
+// sub-partition), and a negated operand reused by several FMAs would
+// otherwise be materialized by an FP64 instruction.  Inline PTX keeps the
+// compiler from turning the XOR back into a floating-point negation.
+__device__ __forceinline__ double neg(double x)
+{
+    double r;
+    asm("{\n\t.reg .b32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\txor.b32 hi, hi, 0x80000000;\n\t"
+        "mov.b64 %0, {lo, hi};\n\t}"
+        : "=d"(r)
+        : "d"(x));
+    return r;
+}
 
 // 64-bit select done on the integer pipe (two 32-bit selects).
 __device__ __forceinline__ double sel(bool c, double a, double b)
@@ -81,6 +105,7 @@ __device__ __forceinline__ bool any_nonfinite(const double (&a)[N][N])
 //            (forward substitution fused into the factorization).
 // piv[k] receives the 0-based pivot row, rcp[k] = RN(1/u_kk) (valid when
 // `tiny` stays false).  Returns info (0 or first zero pivot step + 1).
+// Below the diagonal a holds -l_ik (see lu_thread_unnegate_L).
 template <int N, bool KEEP_L, int NB>
 __device__ __forceinline__ int lu_thread_factor(double (&a)[N][N], double (&b)[NB > 0 ? NB : 1][N],
                                                 int (&piv)[N], double (&rcp)[N], bool &tiny)
@@ -102,6 +127,10 @@ __device__ __forceinline__ int lu_thread_factor(double (&a)[N][N], double (&b)[N
         rcp[k] = 0.0;
         if (best == 0ULL) {
             if (info == 0) info = k + 1;
+            // the column below is zero; store it in the negated convention
+            // too so that the final sign flip restores it bit for bit
+#pragma unroll
+            for (int i = k + 1; i < N; ++i) a[i][k] = neg(a[i][k]);
             continue;
         }
         // a3: physical row interchange k <-> p as a register permutation.
@@ -122,29 +151,52 @@ __device__ __forceinline__ int lu_thread_factor(double (&a)[N][N], double (&b)[N
                 b[c][i] = sel(s, t, b[c][i]);
             }
         }
-        // a4: multipliers with one correctly rounded reciprocal.
+        // a4: multipliers with one correctly rounded reciprocal.  They are
+        // kept NEGATED, -l_ik = RN(a_ik * (-r)) (negation commutes with
+        // rounding), so the update below needs no negated operand.
+        // The quotient path for |pivot| < DBL_MIN is entered by a warp-uniform
+        // branch so that the common path never issues division code.
         const double pv = a[k][k];
-        if (best >= kDblMinBits) {
+        const bool small = best < kDblMinBits;
+        if (!__any_sync(__activemask(), small)) {
             const double r = __drcp_rn(pv);
             rcp[k] = r;
+            const double nr = neg(r);
 #pragma unroll
-            for (int i = k + 1; i < N; ++i) a[i][k] = __dmul_rn(a[i][k], r);
+            for (int i = k + 1; i < N; ++i) a[i][k] = __dmul_rn(a[i][k], nr);
         } else {
-            tiny = true;
+            const double r = __drcp_rn(pv);
+            rcp[k] = r;
+            const double nr = neg(r);
+            const double npv = neg(pv);
+            tiny = tiny || small;
 #pragma unroll
-            for (int i = k + 1; i < N; ++i) a[i][k] = __ddiv_rn(a[i][k], pv);
+            for (int i = k + 1; i < N; ++i)
+                a[i][k] = small ? __ddiv_rn(a[i][k], npv) : __dmul_rn(a[i][k], nr);
         }
-        // a5: rank-1 Schur update; a6 (forward part): b follows as extra columns.
+        // a5: rank-1 Schur update a_ij + (-l_ik) u_kj; a6 (forward part): b
+        // follows as extra columns.
 #pragma unroll
         for (int j = k + 1; j < N; ++j)
 #pragma unroll
-            for (int i = k + 1; i < N; ++i) a[i][j] = __fma_rn(-a[i][k], a[k][j], a[i][j]);
+            for (int i = k + 1; i < N; ++i) a[i][j] = __fma_rn(a[i][k], a[k][j], a[i][j]);
 #pragma unroll
         for (int c = 0; c < NB; ++c)
 #pragma unroll
-            for (int i = k + 1; i < N; ++i) b[c][i] = __fma_rn(-a[i][k], b[c][k], b[c][i]);
+            for (int i = k + 1; i < N; ++i) b[c][i] = __fma_rn(a[i][k], b[c][k], b[c][i]);
     }
     return info;
+}
+
+// lu_thread_factor leaves -l_ik below the diagonal; flip them back to the
+// LAPACK storage of L (integer sign flips only).
+template <int N>
+__device__ __forceinline__ void lu_thread_unnegate_L(double (&a)[N][N])
+{
+#pragma unroll
+    for (int i = 1; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j < i; ++j) a[i][j] = neg(a[i][j]);
 }
 
 // a6 (back part): x_i = (y_i - sum_{j>i} u_ij x_j) * RN(1/u_ii), the sum
@@ -154,21 +206,25 @@ template <int N>
 __device__ __forceinline__ void lu_thread_backsolve(const double (&a)[N][N], double (&y)[N],
                                                     const double (&rcp)[N], bool tiny)
 {
-    if (!tiny) {
+    // nx[j] = -x_j (integer sign flip) so that each step is fma(u_ij, -x_j, s).
+    double nx[N];
+    if (!__any_sync(__activemask(), tiny)) {
 #pragma unroll
         for (int i = N - 1; i >= 0; --i) {
             double s = y[i];
 #pragma unroll
-            for (int j = N - 1; j > i; --j) s = __fma_rn(-a[i][j], y[j], s);
+            for (int j = N - 1; j > i; --j) s = __fma_rn(a[i][j], nx[j], s);
             y[i] = __dmul_rn(s, rcp[i]);
+            nx[i] = neg(y[i]);
         }
     } else {
 #pragma unroll
         for (int i = N - 1; i >= 0; --i) {
             double s = y[i];
 #pragma unroll
-            for (int j = N - 1; j > i; --j) s = __fma_rn(-a[i][j], y[j], s);
-            y[i] = __ddiv_rn(s, a[i][i]);
+            for (int j = N - 1; j > i; --j) s = __fma_rn(a[i][j], nx[j], s);
+            y[i] = tiny ? __ddiv_rn(s, a[i][i]) : __dmul_rn(s, rcp[i]);
+            nx[i] = neg(y[i]);
         }
     }
 }
@@ -190,12 +246,15 @@ __device__ __forceinline__ void lu_thread_forward(const double (&a)[N][N], const
             y[i] = sel(s, t, y[i]);
         }
     }
+    double ny[N];
+    ny[0] = neg(y[0]);
 #pragma unroll
     for (int i = 1; i < N; ++i) {
         double s = y[i];
 #pragma unroll
-        for (int j = 0; j < i; ++j) s = __fma_rn(-a[i][j], y[j], s);
+        for (int j = 0; j < i; ++j) s = __fma_rn(a[i][j], ny[j], s);
         y[i] = s;
+        ny[i] = neg(s);
     }
 }
 
@@ -265,6 +324,8 @@ __device__ __forceinline__ void group_argmax(double &v, int &row)
 // take part in the warp shuffles).
 // On return: pivk[s] = 0-based pivot row of step k = t + s*T (for this
 // lane's steps), rcp[s] = RN(1/u_ii) of this lane's rows, info as usual.
+// The multipliers are left NEGATED below the diagonal (-l_ik); the owner of
+// row i flips columns j < i back when the factors are stored.
 template <int N, int T, bool KEEP_L, int NB>
 __device__ __forceinline__ int lu_group_factor(double (&a)[Group<N, T>::K][N],
                                                double (&b)[Group<N, T>::K],
@@ -334,22 +395,33 @@ __device__ __forceinline__ int lu_group_factor(double (&a)[Group<N, T>::K][N],
         const double r = __drcp_rn(cv);
         if (t == owner_k) rcp[slot_k] = r;
         tiny = tiny || small;
+        // multipliers kept negated (see lu_thread_factor); a zero column is
+        // flipped as well so the final sign flip restores it bit for bit
+        const double nr = neg(r);
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            if (Group<N, T>::slot_alive(s, k)) {
+                const int i = t + s * T;
+                if (zero && i > k && i < N) a[s][k] = neg(a[s][k]);
+            }
+        }
         if (!__any_sync(0xffffffffu, small)) {
 #pragma unroll
             for (int s = 0; s < K; ++s) {
                 if (Group<N, T>::slot_alive(s, k)) {
                     const int i = t + s * T;
                     const bool live = !zero && i > k && i < N;
-                    if (live) a[s][k] = __dmul_rn(a[s][k], r);
+                    if (live) a[s][k] = __dmul_rn(a[s][k], nr);
                 }
             }
         } else {  // some group of the warp has a pivot below DBL_MIN
+            const double ncv = neg(cv);
 #pragma unroll
             for (int s = 0; s < K; ++s) {
                 if (Group<N, T>::slot_alive(s, k)) {
                     const int i = t + s * T;
                     const bool live = !zero && i > k && i < N;
-                    if (live) a[s][k] = small ? __ddiv_rn(a[s][k], cv) : __dmul_rn(a[s][k], r);
+                    if (live) a[s][k] = small ? __ddiv_rn(a[s][k], ncv) : __dmul_rn(a[s][k], nr);
                 }
             }
         }
@@ -365,8 +437,8 @@ __device__ __forceinline__ int lu_group_factor(double (&a)[Group<N, T>::K][N],
                 const bool live = !zero && i > k && i < N;
                 if (live) {
 #pragma unroll
-                    for (int j = k + 1; j < N; ++j) a[s][j] = __fma_rn(-a[s][k], uk[j], a[s][j]);
-                    if (NB > 0) b[s] = __fma_rn(-a[s][k], uk[N], b[s]);
+                    for (int j = k + 1; j < N; ++j) a[s][j] = __fma_rn(a[s][k], uk[j], a[s][j]);
+                    if (NB > 0) b[s] = __fma_rn(a[s][k], uk[N], b[s]);
                 }
             }
         }
@@ -397,11 +469,12 @@ __device__ __forceinline__ void lu_group_backsolve(const double (&a)[Group<N, T>
         }
         xi = __shfl_sync(0xffffffffu, xi, lane0 + owner);
         if (t == owner) b[slot] = xi;
+        const double nxi = neg(xi);
 #pragma unroll
         for (int s = 0; s < K; ++s) {
             if (s * T < i) {  // some lane of this slot has a row below i
                 const int r = t + s * T;
-                if (r < i) b[s] = __fma_rn(-a[s][i], xi, b[s]);
+                if (r < i) b[s] = __fma_rn(a[s][i], nxi, b[s]);
             }
         }
     }

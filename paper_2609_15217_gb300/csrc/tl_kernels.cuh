@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(128) k_factor_thread(SolveArgs args)
         // info = -1: nothing is factored; the factors output keeps A.
         double *LU = args.LU;
         if (!bad) {
+            dev::lu_thread_unnegate_L<N>(a);
 #pragma unroll
             for (int j = 0; j < N; ++j)
 #pragma unroll
@@ -184,7 +185,8 @@ __global__ void __launch_bounds__(128) k_factor_group(SolveArgs args)
             st_stream(args.ipiv + I::v(s, i, args.ld), bad ? i + 1 : pivk[sl] + 1);
             if (KEEP && !bad) {
 #pragma unroll
-                for (int j = 0; j < N; ++j) st_stream(args.LU + I::a(s, i, j, args.ld), a[sl][j]);
+                for (int j = 0; j < N; ++j)
+                    st_stream(args.LU + I::a(s, i, j, args.ld), j < i ? dev::neg(a[sl][j]) : a[sl][j]);
             } else if (KEEP && MODE == kGesv) {
                 for (int j = 0; j < N; ++j) args.LU[I::a(s, i, j, args.ld)] = args.A[I::a(s, i, j, args.ld)];
             }
@@ -256,12 +258,12 @@ __global__ void __launch_bounds__(128) k_getrs_group(SolveArgs args)
         // forward: y_i -= l_ik y_k for i > k, k increasing
 #pragma unroll
         for (int k = 0; k < N - 1; ++k) {
-            const double yk = __shfl_sync(0xffffffffu, y[k / T], lane0 + k % T);
+            const double nyk = dev::neg(__shfl_sync(0xffffffffu, y[k / T], lane0 + k % T));
 #pragma unroll
             for (int sl = 0; sl < K; ++sl) {
                 if (dev::Group<N, T>::slot_alive(sl, k)) {
                     const int i = t + sl * T;
-                    if (i > k && i < N) y[sl] = __fma_rn(-a[sl][k], yk, y[sl]);
+                    if (i > k && i < N) y[sl] = __fma_rn(a[sl][k], nyk, y[sl]);
                 }
             }
         }

@@ -133,16 +133,36 @@ def uniform_systems_torch(n, batch, seed, device, lo=-1.0, hi=1.0):
     return A, b
 
 
-def _haar_torch(g, batch, n, device, chunk=1 << 17):
+def _haar_torch(g, batch, n, device, chunk=1 << 16):
+    """Haar-distributed orthogonal matrices on the device: Householder QR of
+    a Gaussian matrix, Q rebuilt from the reflectors and multiplied by the
+    signs of diag(R) (Mezzadri 2007), all as batched tensor operations."""
     import torch
     out = torch.empty((batch, n, n), dtype=torch.float64, device=device)
-    for s in range(0, batch, chunk):
-        e = min(batch, s + chunk)
-        Z = torch.randn((e - s, n, n), dtype=torch.float64, device=device, generator=g)
-        Q, R = torch.linalg.qr(Z)
-        d = torch.sign(torch.diagonal(R, dim1=1, dim2=2))
-        d[d == 0] = 1.0
-        out[s:e] = Q * d[:, None, :]
+    for c0 in range(0, batch, chunk):
+        c1 = min(batch, c0 + chunk)
+        m = c1 - c0
+        Z = torch.randn((m, n, n), dtype=torch.float64, device=device, generator=g)
+        vs = []
+        rsign = torch.empty((m, n), dtype=torch.float64, device=device)
+        for k in range(n):
+            x = Z[:, k:, k]
+            nx = torch.linalg.vector_norm(x, dim=1)
+            s0 = torch.where(x[:, 0] >= 0, 1.0, -1.0).to(torch.float64)
+            alpha = -s0 * nx                      # R[k, k]
+            v = x.clone()
+            v[:, 0] -= alpha
+            nv = torch.linalg.vector_norm(v, dim=1, keepdim=True)
+            v = torch.where(nv > 0, v / torch.where(nv > 0, nv, 1.0), v)
+            Z[:, k:, k:] -= 2.0 * v[:, :, None] * torch.einsum("bi,bij->bj", v, Z[:, k:, k:])[:, None, :]
+            vs.append(v)
+            rsign[:, k] = torch.where(alpha >= 0, 1.0, -1.0)
+        Q = torch.eye(n, dtype=torch.float64, device=device).expand(m, n, n).clone()
+        for k in range(n - 1, -1, -1):
+            v = vs[k]
+            Q[:, k:, :] -= 2.0 * v[:, :, None] * torch.einsum("bi,bij->bj", v, Q[:, k:, :])[:, None, :]
+        out[c0:c1] = Q * rsign[:, None, :]
+        del Z, Q, vs
     return out
 
 
