@@ -11,12 +11,6 @@ tl_status tl_lupp_solve_batched(tl_handle *h, int64_t, const int32_t *, const in
     return h ? TL_ERR_UNSUPPORTED : TL_ERR_INVALID_ARG;
 }
 
-tl_status tl_newton_integrate(tl_handle *h, const tl_law *, int64_t, const double *, double *, double *,
-                              int32_t *, int32_t *, double, int, cudaStream_t)
-{
-    return h ? TL_ERR_UNSUPPORTED : TL_ERR_INVALID_ARG;
-}
-
 tl_status tl_autotune(tl_handle *h, int, int, tl_layout, const char *)
 {
     return h ? TL_ERR_UNSUPPORTED : TL_ERR_INVALID_ARG;

@@ -1,0 +1,131 @@
+"""GPU parity of the fused per-point Newton kernel (tl_newton_integrate,
+Algorithm 2 / Eqs. 1-3) against the oracle's Newton driver.
+
+Bar: identical iteration counts and status for every point whose stopping
+decisions are not within 1e-6 (relative) of the threshold (the oracle flags
+those), and final states within 1e-10 relative (normwise per point).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2609_15217_gb300 import inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def tl():
+    from paper_2609_15217_gb300 import tinylu
+    return tinylu
+
+
+@pytest.fixture(scope="module")
+def h(tl):
+    hh = tl.tl_create()
+    yield hh
+    tl.tl_destroy(hh)
+
+
+def gpu_norton(tl, h, prm, sig0, deps, rtol=1e-10, max_iter=20, want_sig=True):
+    npts = sig0.shape[0]
+    fields = np.ascontiguousarray(np.concatenate([sig0.T, deps.T], axis=0))  # (12, npts)
+    d_in = torch.from_numpy(fields).to(DEV)
+    d_x = torch.full((7, npts), -7.0, dtype=torch.float64, device=DEV)
+    d_sig = torch.full((6, npts), -7.0, dtype=torch.float64, device=DEV) if want_sig else None
+    d_it = torch.full((npts,), -7, dtype=torch.int32, device=DEV)
+    d_st = torch.full((npts,), -7, dtype=torch.int32, device=DEV)
+    law = tl.make_law(tl.TL_LAW_NORTON, 7, prm)
+    tl.check("tl_newton_integrate", tl.tl_newton_integrate(h, law, npts, d_in, d_x, d_sig, d_it, d_st, rtol, max_iter), h)
+    torch.cuda.synchronize()
+    return (d_x.cpu().numpy().T, d_it.cpu().numpy(), d_st.cpu().numpy(),
+            d_sig.cpu().numpy().T if want_sig else None)
+
+
+def compare_states(x_g, x_o, tol=1e-10):
+    scale = np.maximum(np.abs(x_o).max(axis=1), 1e-300)
+    err = np.abs(x_g - x_o).max(axis=1) / scale
+    assert (err <= tol).all(), f"max relative state difference {err.max():.3g}"
+
+
+@pytest.mark.parametrize("npts", [1, 31, 20000 + 37])
+def test_norton_parity(tl, h, npts):
+    prm = oracle.norton_params()
+    sig0, deps = inputs.norton_points(npts, inputs.config_seed(3) + npts)
+    r = oracle.newton_norton(prm, sig0, deps, rtol=1e-10, max_iter=20)
+    x_g, it_g, st_g, sig_g = gpu_norton(tl, h, prm, sig0, deps)
+    flagged = r["rmin_ratio"] < 1e-6
+    ok = ~flagged
+    assert flagged.sum() <= max(1, npts // 1000)
+    assert np.array_equal(it_g[ok], r["iterations"][ok])
+    assert np.array_equal(st_g[ok], r["status"][ok])
+    assert (st_g == 0).all()
+    compare_states(x_g[ok], r["x"][ok])
+    compare_states(sig_g[ok], r["sig"][ok])
+
+
+def test_norton_special_cases(tl, h):
+    npts = 500
+    sig0, deps = inputs.norton_points(npts, 31)
+    # elastic: A = 0 -> zero residual at the predictor, no solve
+    prm0 = oracle.norton_params(A=0.0)
+    x_g, it_g, st_g, _ = gpu_norton(tl, h, prm0, sig0, deps)
+    assert (it_g == 0).all() and (st_g == 0).all()
+    assert np.array_equal(x_g[:, :6], deps) and (x_g[:, 6] == 0).all()
+    # iteration cap: the state after exactly two solves matches the oracle's
+    prm = oracle.norton_params()
+    r = oracle.newton_norton(prm, sig0, deps, rtol=1e-10, max_iter=2)
+    x_g, it_g, st_g, _ = gpu_norton(tl, h, prm, sig0, deps, max_iter=2)
+    assert np.array_equal(it_g, r["iterations"]) and np.array_equal(st_g, r["status"])
+    assert (st_g == 1).sum() > npts // 2
+    compare_states(x_g, r["x"])
+    # max_iter = 0: status 1 with the predictor returned
+    x_g, it_g, st_g, _ = gpu_norton(tl, h, prm, sig0, deps, max_iter=0)
+    assert (it_g == 0).all() and (st_g == 1).all()
+    # non-finite inputs -> status 3
+    sig_bad = sig0.copy()
+    sig_bad[::7, 2] = np.nan
+    _, _, st_g, _ = gpu_norton(tl, h, prm, sig_bad, deps)
+    assert (st_g[::7] == 3).all()
+    # no stress output requested
+    x_g2, it_g2, st_g2, _ = gpu_norton(tl, h, prm, sig0, deps, want_sig=False)
+    r = oracle.newton_norton(prm, sig0, deps)
+    compare_states(x_g2, r["x"])
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 7, 9])
+def test_tanh_parity(tl, h, n):
+    npts = 3000 + 13
+    A, c, b = inputs.tanh_points(n, npts, 900 + n)
+    r = oracle.newton_tanh(A, c, b, rtol=1e-10, max_iter=20)
+    Acm = A.transpose(0, 2, 1).reshape(npts, n * n)           # column-major fields
+    fields = np.ascontiguousarray(np.concatenate([Acm.T, c.T, b.T], axis=0))
+    d_in = torch.from_numpy(fields).to(DEV)
+    d_x = torch.empty((n, npts), dtype=torch.float64, device=DEV)
+    d_it = torch.empty(npts, dtype=torch.int32, device=DEV)
+    d_st = torch.empty(npts, dtype=torch.int32, device=DEV)
+    law = tl.make_law(tl.TL_LAW_TANH, n)
+    tl.check("tanh", tl.tl_newton_integrate(h, law, npts, d_in, d_x, None, d_it, d_st, 1e-10, 20), h)
+    torch.cuda.synchronize()
+    ok = r["rmin_ratio"] >= 1e-6
+    assert np.array_equal(d_it.cpu().numpy()[ok], r["iterations"][ok])
+    assert np.array_equal(d_st.cpu().numpy()[ok], r["status"][ok])
+    compare_states(d_x.cpu().numpy().T[ok], r["x"][ok])
+
+
+def test_newton_argument_errors(tl, h):
+    d = torch.zeros(64, dtype=torch.float64, device=DEV)
+    i = torch.zeros(64, dtype=torch.int32, device=DEV)
+    law = tl.make_law(tl.TL_LAW_NORTON, 6, oracle.norton_params())
+    assert tl.tl_newton_integrate(h, law, 4, d, d, None, i, i, 1e-10, 20) == tl.TL_ERR_INVALID_ARG
+    law = tl.make_law(tl.TL_LAW_NORTON, 7, oracle.norton_params(m=2.5))
+    assert tl.tl_newton_integrate(h, law, 4, d, d, None, i, i, 1e-10, 20) == tl.TL_ERR_INVALID_ARG
+    law = tl.make_law(tl.TL_LAW_NORTON, 7, oracle.norton_params())
+    assert tl.tl_newton_integrate(h, law, 4, d, d, None, i, i, -1.0, 20) == tl.TL_ERR_INVALID_ARG
+    assert tl.tl_newton_integrate(h, law, 4, d, d, None, i, i, 1e-10, -1) == tl.TL_ERR_INVALID_ARG
+    assert tl.tl_newton_integrate(h, law, 0, d, d, None, i, i, 1e-10, 20) == tl.TL_OK
+    law = tl.make_law(99, 7)
+    assert tl.tl_newton_integrate(h, law, 4, d, d, None, i, i, 1e-10, 20) == tl.TL_ERR_INVALID_ARG
