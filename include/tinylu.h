@@ -173,8 +173,13 @@ tl_status tl_gesv_batched(tl_handle *h, int n, const double *A, double *LU_out, 
  *           refine_steps)
  *   refine_steps  nullable device int32[batch]: refinement steps taken
  *           (FP32_IR), -1 when the system fell back to a binary64 factor.
- * Systems are bucketed by n on the device (handle workspace) and solved by
- * the per-n kernels of tl_gesv_batched.
+ * info[s] = -2 when n[s] is outside 1..32 (that system is skipped, its x
+ * and ipiv are not written); otherwise as for tl_gesv_batched.
+ * Systems are bucketed by n on the device in the handle's workspace (grown
+ * on demand with cudaMalloc; a call that would need to grow it while the
+ * stream is being captured returns TL_ERR_NO_MEMORY) and solved by the
+ * per-n kernels of tl_gesv_batched, one persistent launch per n.  batch must
+ * be below 2^31.  TL_PREC_FP32_IR returns TL_ERR_UNSUPPORTED in this build.
  */
 tl_status tl_lupp_solve_batched(tl_handle *h, int64_t batch, const int32_t *n, const int64_t *a_off,
                                 const double *A, const int64_t *b_off, const double *b, double *x,

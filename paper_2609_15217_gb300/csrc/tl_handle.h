@@ -32,6 +32,11 @@ tl_status fail_cuda(tl_handle *h, cudaError_t e);
 int pick_block(tl_handle *h, const void *kernel, int64_t threads);
 tl_status launch_variant(tl_handle *h, const Variant *v, int block, SolveArgs &args, cudaStream_t stream);
 tl_status launch_op(tl_handle *h, int n, int layout, int op, SolveArgs &args, cudaStream_t stream);
+tl_status ensure_workspace(tl_handle *h, size_t bytes, cudaStream_t stream);
+// Buckets `batch` systems by n[s] using the int32 scratch `ws` (3*64 bin
+// counters followed by `batch` indices) and launches the per-n kernels.
+tl_status ragged_solve(tl_handle *h, int64_t batch, const int32_t *n, RaggedArgs r, int32_t *ws,
+                       cudaStream_t stream);
 
 }  // namespace tl
 

@@ -35,6 +35,13 @@ struct Registrar {
     {
         reg_one_layout<TL_INST_N, TL_INST_T, kPerSystem>();
         reg_one_layout<TL_INST_N, TL_INST_T, kInterleaved>();
+        // ragged batches are per-system storage only; registered in slot 0
+        if constexpr (TL_INST_T == 1)
+            register_variant(TL_INST_N, kPerSystem, kOpRagged, 1,
+                             reinterpret_cast<const void *>(&k_ragged_thread<TL_INST_N>));
+        else
+            register_variant(TL_INST_N, kPerSystem, kOpRagged, TL_INST_T,
+                             reinterpret_cast<const void *>(&k_ragged_group<TL_INST_N, TL_INST_T>));
     }
 };
 const Registrar registrar_instance;

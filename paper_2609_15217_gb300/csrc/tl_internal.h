@@ -25,6 +25,22 @@ struct SolveArgs {
     int nrhs;
 };
 
+// Arguments of the ragged-batch kernels (tl_lupp_solve_batched): the
+// systems of size N are listed in bucket[offsets[N] .. offsets[N+1]); each
+// one lives at its own element offsets in per-system column-major storage.
+struct RaggedArgs {
+    const int32_t *bucket;
+    const int32_t *offsets;  // [TL_MAX_N + 2]
+    const int64_t *a_off;
+    const double *A;
+    const int64_t *b_off;
+    const double *b;
+    double *x;
+    const int64_t *piv_off;
+    int32_t *ipiv;
+    int32_t *info;
+};
+
 // Kernel variant for one (n, layout, operation): how many lanes share a
 // system (1 = one thread per system) and the launch entry.
 struct Variant {
@@ -34,8 +50,8 @@ struct Variant {
 };
 
 // Registry filled by the instantiation units (tl_inst.cu, one per (N, T)).
-enum : int { kOpGesv = 0, kOpGesvLU = 1, kOpGetrf = 2, kOpGetrs = 3 };
-constexpr int kOps = 4;
+enum : int { kOpGesv = 0, kOpGesvLU = 1, kOpGetrf = 2, kOpGetrs = 3, kOpRagged = 4 };
+constexpr int kOps = 5;
 constexpr int kMaxVariants = 6;
 struct VariantList {
     int count;

@@ -278,4 +278,98 @@ __global__ void __launch_bounds__(128) k_getrs_group(SolveArgs args)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Ragged batches (tl_lupp_solve_batched): persistent grid-stride kernels over
+// the bucket of systems of size N, each system at its own offsets.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(128) k_ragged_thread(RaggedArgs r)
+{
+    const int64_t beg = r.offsets[N];
+    const int64_t count = r.offsets[N + 1] - beg;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < count; q += stride) {
+        const int64_t s = r.bucket[beg + q];
+        const double *A = r.A + r.a_off[s];
+        const double *bv = r.b + r.b_off[s];
+        double a[N][N];
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+#pragma unroll
+            for (int i = 0; i < N; ++i) a[i][j] = ld_stream(A + (j * N + i));
+        double b[1][N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) b[0][i] = ld_stream(bv + i);
+        const bool bad = dev::any_nonfinite<N>(a);
+        int piv[N];
+        double rcp[N];
+        bool tiny = false;
+        int info = dev::lu_thread_factor<N, false, 1>(a, b, piv, rcp, tiny);
+        dev::lu_thread_backsolve<N>(a, b[0], rcp, tiny);
+        if (bad) info = -1;
+        double *x = r.x + r.b_off[s];
+        int32_t *ip = r.ipiv + r.piv_off[s];
+#pragma unroll
+        for (int i = 0; i < N; ++i) st_stream(x + i, info != 0 ? dev::nan_value() : b[0][i]);
+#pragma unroll
+        for (int k = 0; k < N; ++k) st_stream(ip + k, bad ? k + 1 : piv[k] + 1);
+        st_stream(r.info + s, info);
+    }
+}
+
+template <int N, int T>
+__global__ void __launch_bounds__(128) k_ragged_group(RaggedArgs r)
+{
+    constexpr int K = dev::Group<N, T>::K;
+    constexpr int G = 32 / T;  // systems per warp
+    const int lane = threadIdx.x & 31;
+    const int t = lane % T;
+    const int lane0 = lane - t;
+    const int64_t beg = r.offsets[N];
+    const int64_t count = r.offsets[N + 1] - beg;
+    const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t q0 = warp * G; q0 < count; q0 += nwarps * G) {  // warp-uniform loop
+        const int64_t q = q0 + lane / T;
+        const bool active = q < count;
+        const int64_t s = active ? r.bucket[beg + q] : 0;
+        const double *A = r.A + (active ? r.a_off[s] : 0);
+        double a[K][N];
+        double b[K];
+#pragma unroll
+        for (int sl = 0; sl < K; ++sl) {
+            const int i = t + sl * T;
+            const bool ok = active && i < N;
+#pragma unroll
+            for (int j = 0; j < N; ++j) a[sl][j] = ok ? A[j * N + i] : 0.0;
+            b[sl] = ok ? ld_stream(r.b + r.b_off[s] + i) : 0.0;
+        }
+        bool mybad = false;
+#pragma unroll
+        for (int sl = 0; sl < K; ++sl)
+#pragma unroll
+            for (int j = 0; j < N; ++j) mybad |= dev::is_nonfinite(a[sl][j]);
+        const bool bad = group_any<T>(mybad);
+        int pivk[K];
+        double rcp[K];
+        bool tiny = false;
+        int info = dev::lu_group_factor<N, T, false, 1>(a, b, pivk, rcp, t, lane0, tiny);
+        dev::lu_group_backsolve<N, T>(a, b, rcp, t, lane0, tiny);
+        if (bad) info = -1;
+        if (active) {
+            double *x = r.x + r.b_off[s];
+            int32_t *ip = r.ipiv + r.piv_off[s];
+#pragma unroll
+            for (int sl = 0; sl < K; ++sl) {
+                const int i = t + sl * T;
+                if (i < N) {
+                    st_stream(x + i, info != 0 ? dev::nan_value() : b[sl]);
+                    st_stream(ip + i, bad ? i + 1 : pivk[sl] + 1);
+                }
+            }
+            if (t == 0) st_stream(r.info + s, info);
+        }
+    }
+}
+
 }  // namespace tl

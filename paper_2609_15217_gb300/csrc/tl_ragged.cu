@@ -1,0 +1,173 @@
+// tl_ragged.cu -- tl_lupp_solve_batched: a batch whose systems have their
+// own sizes n[s] (1..32) and their own places in memory.
+//
+// The systems are bucketed by n on the device (histogram, exclusive scan,
+// block-aggregated scatter of the system indices into the handle's
+// workspace), then one persistent grid-stride launch per n solves its bucket
+// with the same per-n kernels as tl_gesv_batched.  No host synchronization:
+// the bucket sizes stay on the device and every launch reads them there.
+#include <climits>
+
+#include "tinylu.h"
+#include "tl_handle.h"
+#include "tl_internal.h"
+
+namespace tl {
+namespace {
+
+constexpr int kSlots = 64;  // per-bin arrays, indices 0..TL_MAX_N+1 used
+
+__global__ void k_bucket_hist(int64_t batch, const int32_t *__restrict__ n, int32_t *__restrict__ counts,
+                              int32_t *__restrict__ info)
+{
+    __shared__ int32_t sh[kSlots];
+    if (threadIdx.x < kSlots) sh[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (s < batch) {
+        const int v = n[s];
+        if (v >= 1 && v <= TL_MAX_N) atomicAdd(&sh[v], 1);
+        else info[s] = -2;
+    }
+    __syncthreads();
+    if (threadIdx.x >= 1 && threadIdx.x <= TL_MAX_N && sh[threadIdx.x] > 0)
+        atomicAdd(&counts[threadIdx.x], sh[threadIdx.x]);
+}
+
+// offsets[v] = number of systems with size < v (v = 1..TL_MAX_N+1)
+__global__ void k_bucket_scan(const int32_t *__restrict__ counts, int32_t *__restrict__ offsets,
+                              int32_t *__restrict__ cursor)
+{
+    if (threadIdx.x != 0) return;
+    int32_t acc = 0;
+    offsets[0] = 0;
+    for (int v = 1; v <= TL_MAX_N + 1; ++v) {
+        offsets[v] = acc;
+        cursor[v] = acc;
+        if (v <= TL_MAX_N) acc += counts[v];
+    }
+}
+
+__global__ void k_bucket_scatter(int64_t batch, const int32_t *__restrict__ n, int32_t *__restrict__ cursor,
+                                 int32_t *__restrict__ bucket)
+{
+    __shared__ int32_t sh[kSlots];
+    __shared__ int32_t base[kSlots];
+    if (threadIdx.x < kSlots) sh[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    int v = 0, rank = 0;
+    if (s < batch) {
+        v = n[s];
+        if (v >= 1 && v <= TL_MAX_N) rank = atomicAdd(&sh[v], 1);
+        else v = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x >= 1 && threadIdx.x <= TL_MAX_N && sh[threadIdx.x] > 0)
+        base[threadIdx.x] = atomicAdd(&cursor[threadIdx.x], sh[threadIdx.x]);
+    __syncthreads();
+    if (v > 0) bucket[base[v] + rank] = static_cast<int32_t>(s);
+}
+
+}  // namespace
+
+// Grow the handle's device workspace to at least `bytes`.  Never allocates
+// while `stream` is being captured into a graph.
+tl_status ensure_workspace(tl_handle *h, size_t bytes, cudaStream_t stream)
+{
+    if (h->ws_bytes >= bytes) return TL_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusNone;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return TL_ERR_NO_MEMORY;
+    if (h->ws) {
+        cudaError_t e = cudaDeviceSynchronize();  // earlier calls may still read it
+        if (e != cudaSuccess) return fail_cuda(h, e);
+        cudaFree(h->ws);
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+    }
+    size_t want = bytes < (size_t(1) << 20) ? (size_t(1) << 20) : bytes;
+    if (cudaMalloc(&h->ws, want) != cudaSuccess) {
+        cudaGetLastError();
+        h->ws = nullptr;
+        return TL_ERR_NO_MEMORY;
+    }
+    h->ws_bytes = want;
+    return TL_OK;
+}
+
+// Bucket the batch by size and launch every per-n ragged kernel.  `ws` holds
+// 3 * kSlots int32 bin arrays followed by `batch` int32 indices.
+tl_status ragged_solve(tl_handle *h, int64_t batch, const int32_t *n, RaggedArgs r, int32_t *ws,
+                       cudaStream_t stream)
+{
+    int32_t *counts = ws;
+    int32_t *offsets = ws + kSlots;
+    int32_t *cursor = ws + 2 * kSlots;
+    int32_t *bucket = ws + 3 * kSlots;
+    cudaError_t e = cudaMemsetAsync(counts, 0, kSlots * sizeof(int32_t), stream);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    const int block = 256;
+    const unsigned grid = static_cast<unsigned>((batch + block - 1) / block);
+    k_bucket_hist<<<grid, block, 0, stream>>>(batch, n, counts, r.info);
+    k_bucket_scan<<<1, 32, 0, stream>>>(counts, offsets, cursor);
+    k_bucket_scatter<<<grid, block, 0, stream>>>(batch, n, cursor, bucket);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(h, e);
+    r.bucket = bucket;
+    r.offsets = offsets;
+    for (int nn = 1; nn <= TL_MAX_N; ++nn) {
+        const Choice &c = h->choice[nn][kPerSystem][kOpRagged];
+        const Variant *v = find_variant(nn, kPerSystem, kOpRagged, c.lanes ? c.lanes : default_lanes(nn));
+        if (!v) return TL_ERR_UNSUPPORTED;
+        const int blk = 128;
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, v->kernel, blk, 0) != cudaSuccess || nb < 1) {
+            cudaGetLastError();
+            nb = 1;
+        }
+        int64_t need = (batch * v->lanes + blk - 1) / blk;
+        int64_t resident = static_cast<int64_t>(nb) * h->sm_count;
+        int64_t g = need < resident ? need : resident;
+        void *params[] = {&r};
+        e = cudaLaunchKernel(v->kernel, dim3(static_cast<unsigned>(g)), dim3(blk), params, 0, stream);
+        if (e != cudaSuccess) return fail_cuda(h, e);
+    }
+    return TL_OK;
+}
+
+}  // namespace tl
+
+using namespace tl;
+
+extern "C" tl_status tl_lupp_solve_batched(tl_handle *h, int64_t batch, const int32_t *n, const int64_t *a_off,
+                                           const double *A, const int64_t *b_off, const double *b, double *x,
+                                           const int64_t *piv_off, int32_t *ipiv, int32_t *info,
+                                           tl_precision prec, int32_t *refine_steps, cudaStream_t stream)
+{
+    if (!h) return TL_ERR_INVALID_ARG;
+    h->last_bad_arg = 0;
+    if (batch < 0) return fail_arg(h, 2);
+    if (prec != TL_PREC_FP64 && prec != TL_PREC_FP32_IR) return fail_arg(h, 12);
+    if (batch == 0) return TL_OK;
+    auto mis = [](const void *p, size_t a) { return !p || (reinterpret_cast<uintptr_t>(p) % a) != 0; };
+    if (mis(n, 4)) return fail_arg(h, 3);
+    if (mis(a_off, 8)) return fail_arg(h, 4);
+    if (mis(A, 8)) return fail_arg(h, 5);
+    if (mis(b_off, 8)) return fail_arg(h, 6);
+    if (mis(b, 8)) return fail_arg(h, 7);
+    if (mis(x, 8)) return fail_arg(h, 8);
+    if (mis(piv_off, 8)) return fail_arg(h, 9);
+    if (mis(ipiv, 4)) return fail_arg(h, 10);
+    if (mis(info, 4)) return fail_arg(h, 11);
+    if (refine_steps && (reinterpret_cast<uintptr_t>(refine_steps) & 3)) return fail_arg(h, 13);
+    if (prec == TL_PREC_FP32_IR) return TL_ERR_UNSUPPORTED;
+    if (batch > INT32_MAX) return TL_ERR_UNSUPPORTED;
+    const size_t bytes = (3 * kSlots + static_cast<size_t>(batch)) * sizeof(int32_t);
+    tl_status st = ensure_workspace(h, bytes, stream);
+    if (st != TL_OK) return st;
+    RaggedArgs r{nullptr, nullptr, a_off, A, b_off, b, x, piv_off, ipiv, info};
+    return ragged_solve(h, batch, n, r, static_cast<int32_t *>(h->ws), stream);
+}
