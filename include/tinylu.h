@@ -187,6 +187,39 @@ tl_status tl_lupp_solve_batched(tl_handle *h, int64_t batch, const int32_t *n, c
                                 tl_precision prec, int32_t *refine_steps, cudaStream_t stream);
 
 /*
+ * tl_lupp_solve_batched_noalloc -- the ragged solve of tl_lupp_solve_batched
+ * (FP64 only) for callers that must not allocate device memory.  The paper
+ * has no counterpart; this entry exists for the library's users.
+ *
+ * tl_lupp_solve_batched keeps its per-size index lists in a workspace the
+ * handle grows with cudaMalloc, which also synchronizes the whole device and
+ * frees the old buffer.  Callers that run under a device-memory budget owned
+ * by someone else, latency-bound serving loops that must never stall the
+ * device, and code that may not synchronize other GPU work cannot accept
+ * that.  This call uses instead a fixed scratch array built into the
+ * library: it never calls cudaMalloc, cudaFree or any allocating routine.
+ *
+ *   batch  at most TL_NOALLOC_MAX_BATCH systems; a larger batch returns
+ *          TL_ERR_INVALID_ARG with tl_last_bad_arg() == 2 and launches
+ *          nothing.  Other arguments and results as tl_lupp_solve_batched.
+ *   The scratch array (TL_NOALLOC_MAX_BATCH + 192 int32, about 4 MiB) exists
+ *   on every GPU that loads the library, from load until process exit.
+ *   The first call with a given device current looks up the array's device
+ *   address (cudaGetSymbolAddress) and caches it; make that first call
+ *   before any stream capture on that device.
+ *   Every call on a device shares the one array and its counters are
+ *   cleared at the start of each call on `stream`: calls that may overlap on
+ *   the GPU (different streams, or different host threads) race and must be
+ *   serialized by the caller, e.g. by issuing them on one stream.
+ */
+#define TL_NOALLOC_MAX_BATCH (1 << 20)
+tl_status tl_lupp_solve_batched_noalloc(tl_handle *h, int64_t batch, const int32_t *n,
+                                        const int64_t *a_off, const double *A,
+                                        const int64_t *b_off, const double *b, double *x,
+                                        const int64_t *piv_off, int32_t *ipiv, int32_t *info,
+                                        cudaStream_t stream);
+
+/*
  * tl_newton_integrate -- one fused kernel runs every point's own Newton loop
  * (Algorithm 2; Eqs. 1-3 of Sec. 2.1): assemble F and J, solve
  * J dx = -F by the in-register LUpp, x += dx, test convergence.

@@ -45,6 +45,7 @@ _SIGS = {
     "tl_getrs_batched": ([_vp, _int, _int, _vp, _vp, _int, _i64, _vp, _i64, _vp], _int),
     "tl_gesv_batched": ([_vp, _int, _vp, _vp, _vp, _vp, _vp, _vp, _int, _i64, _i64, _vp], _int),
     "tl_lupp_solve_batched": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _int, _vp, _vp], _int),
+    "tl_lupp_solve_batched_noalloc": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _int),
     "tl_newton_integrate": ([_vp, C.POINTER(tl_law), _i64, _vp, _vp, _vp, _vp, _vp, C.c_double, _int, _vp], _int),
     "tl_autotune": ([_vp, _int, _int, _int, C.c_char_p], _int),
 }
@@ -142,6 +143,14 @@ def tl_lupp_solve_batched(h, batch, n, a_off, A, b_off, b, x, piv_off, ipiv, inf
                           refine_steps=None, stream=None):
     return _lib.tl_lupp_solve_batched(h, batch, _p(n), _p(a_off), _p(A), _p(b_off), _p(b), _p(x), _p(piv_off),
                                       _p(ipiv), _p(info), prec, _p(refine_steps), _stream(stream))
+
+
+def tl_lupp_solve_batched_noalloc(h, batch, n, a_off, A, b_off, b, x, piv_off, ipiv, info, stream=None):
+    return _lib.tl_lupp_solve_batched_noalloc(h, batch, _p(n), _p(a_off), _p(A), _p(b_off), _p(b), _p(x),
+                                              _p(piv_off), _p(ipiv), _p(info), _stream(stream))
+
+
+TL_NOALLOC_MAX_BATCH = 1 << 20
 
 
 def make_law(law_id, n, params=()):
