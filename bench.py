@@ -67,6 +67,12 @@ def bytes_per_system(n):
 FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12
 
 
+# DRAM bytes per system measured by ncu for the current kernels
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch / systems);
+# an entry must be removed whenever its kernel changes.
+DRAM_BYTES_PER_SYSTEM = {8: 651, 32: 8843}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -134,11 +140,11 @@ class Clocks:
 # workload
 # ---------------------------------------------------------------------------
 
-def make_sweep(n_list, layout, seed_base, device, torch, L, I):
+def make_sweep(n_list, layout, seed_base, device, torch, L, I, cap=None):
     """Generate every n's batch on the device and pack it in `layout`."""
     data = {}
     for n in n_list:
-        S = sweep_batch(n)
+        S = sweep_batch(n) if cap is None else min(cap, sweep_batch(n))
         log(f"generate n={n} batch={S} layout={layout}")
         A, b, _x = I.sweep_systems_torch(n, S, seed_base * 1000 + n, device)
         ld = L.pad_ld(S)
@@ -251,6 +257,57 @@ def sweep_e2e(tl, h, n_list, layout, steps, warmup, torch, device, L):
             "inputs": "one pinned host pool of U[-1,1] entries (sized for the largest n) backs every n's A and b"}
 
 
+# FP64 flops of one Norton law evaluation with its Jacobian and the residual
+# norm: every operation on a value that depends on the point's data, counted
+# on the oracle's code (sqrt and division count 1, parameter-only products
+# excluded): strain trace 2, stress 18, mean stress 3, deviator 3, s:s 12,
+# seq 2, flow direction 12, powers 4, residual 20, Jacobian 153 (c 2,
+# 36 x (n_i n_j, 1.5K - nn, c*v, +delta) 144, g 1, last row 6), norm 15.
+NORTON_EVAL_FLOPS = 244
+NORTON_LU_FLOPS = flops_per_system(7)
+
+
+def newton_bench(tl, h, steps, warmup, torch, device, I, seed, npoints=NEWTON_POINTS):
+    """Fused Norton Newton over npoints (n = 7): points/s and FP64 fraction."""
+    sig0, deps = I.norton_points_torch(npoints, seed, device)
+    fields = torch.cat([sig0.t(), deps.t()], dim=0).contiguous()  # (12, npoints)
+    del sig0, deps
+    x = torch.empty((7, npoints), dtype=torch.float64, device=device)
+    sig = torch.empty((6, npoints), dtype=torch.float64, device=device)
+    it = torch.empty(npoints, dtype=torch.int32, device=device)
+    st = torch.empty(npoints, dtype=torch.int32, device=device)
+    law = tl.make_law(tl.TL_LAW_NORTON, 7, (200000.0, 0.3, 1e-12, 4.0, 1.0))
+    stream = torch.cuda.current_stream()
+
+    def run():
+        r = tl.tl_newton_integrate(h, law, npoints, fields, x, sig, it, st, 1e-10, 20, stream.cuda_stream)
+        if r != 0:
+            tl.check("tl_newton_integrate", r, h)
+
+    for _ in range(warmup):
+        run()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(steps):
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    med = statistics.median(ms)
+    iters = it.to(torch.int64)
+    total_it = int(iters.sum().item())
+    flops = total_it * NORTON_LU_FLOPS + (total_it + npoints) * NORTON_EVAL_FLOPS
+    status = torch.bincount(st.to(torch.int64), minlength=4).tolist()
+    return {"points": npoints, "ms": med, "points_per_s": npoints / (med / 1e3),
+            "mean_iterations": total_it / npoints, "max_iterations": int(iters.max().item()),
+            "status_counts": status[:4], "fp64_tflops": flops / (med / 1e3) / 1e12,
+            "fp64_frac": flops / (med / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+            "flops_model": "per solve 300 (LU n=7) + per law evaluation 244"}
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
@@ -327,6 +384,9 @@ def main():
     ap.add_argument("--no-per-system", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-newton", action="store_true")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="cap on systems per n (small cases for profiling; the default is the full sweep)")
     ap.add_argument("--ref-seconds-per-n", type=float, default=0.3)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -355,7 +415,7 @@ def main():
     h = tl.tl_create()
     n_list = list(range(args.nmin, args.nmax + 1))
     t_gen = time.perf_counter()
-    data = make_sweep(n_list, 1, 1236 + 100 * rank, device, torch, L, I)
+    data = make_sweep(n_list, 1, 1236 + 100 * rank, device, torch, L, I, args.batch)
     gen_s = time.perf_counter() - t_gen
 
     log("timing interleaved sweep")
@@ -382,11 +442,17 @@ def main():
                         "fp64_frac": f / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
                         "gbs": bytes_per_system(n) * d["S"] / (ms / 1e3) / 1e9}
     dom = max(per_n_out, key=lambda n: per_n_out[n]["ms"])
+    if 32 in per_n_out and per_n_out[32]["ms"] >= 0.97 * per_n_out[dom]["ms"]:
+        dom = 32  # the n=25..32 launches take equal shares; n=32 is the profiled one
     dom_flops = flops_per_system(dom) * data[dom]["S"]
     achieved = dom_flops / (per_n_out[dom]["ms"] / 1e3) / 1e12
+    traffic = DRAM_BYTES_PER_SYSTEM.get(dom)
     roofline = {"bound": "alu", "pipe": "fp64", "kernel": f"gesv n={dom} interleaved",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": traffic * data[dom]["S"] if traffic else None,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per system, scaled to the launch"
+                if traffic else None,
                 "peak_source": "derived: 152 SMs x 4 SMSPs x 0.5 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25)",
                 "sweep_fp64_frac": flops_total / (med_step / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
     del data
@@ -395,7 +461,7 @@ def main():
     extra = {}
     if not args.no_per_system:
         log("per-system layout sweep")
-        data_ps = make_sweep(n_list, 0, 1236 + 100 * rank, device, torch, L, I)
+        data_ps = make_sweep(n_list, 0, 1236 + 100 * rank, device, torch, L, I, args.batch)
         ms_ps, per_n_ps = time_sweep(tl, h, data_ps, 0, max(2, args.steps // 2), 1, torch, barrier)
         sys_ps = sum(d["S"] for d in data_ps.values())
         extra["per_system_layout"] = {
@@ -403,6 +469,12 @@ def main():
             "ms_per_step": statistics.median(ms_ps),
             "per_n_solves_per_s": {n: data_ps[n]["S"] / (statistics.median(per_n_ps[n]) / 1e3) for n in data_ps}}
         del data_ps
+        torch.cuda.empty_cache()
+
+    if not args.no_newton:
+        log("newton")
+        extra["newton"] = newton_bench(tl, h, max(2, args.steps // 2), 2, torch, device, I, 1237 + 100 * rank)
+        extra["newton"]["points_per_s"] *= world
         torch.cuda.empty_cache()
 
     e2e = None
