@@ -13,6 +13,7 @@
 #include "tinylu.h"
 #include "tl_handle.h"
 #include "tl_internal.h"
+#include "tl_smem.cuh"
 
 namespace tl {
 
@@ -23,19 +24,19 @@ static VariantList g_registry[TL_MAX_N + 1][2][kOps];
 
 VariantList &registry(int n, int layout, int op) { return g_registry[n][layout][op]; }
 
-void register_variant(int n, int layout, int op, int lanes, const void *kernel)
+void register_variant(int n, int layout, int op, int lanes, const void *kernel, int kind)
 {
     if (n < 1 || n > TL_MAX_N || layout < 0 || layout > 1 || op < 0 || op >= kOps) return;
     VariantList &l = g_registry[n][layout][op];
     for (int i = 0; i < l.count; ++i)
-        if (l.v[i].lanes == lanes) return;
-    if (l.count < kMaxVariants) l.v[l.count++] = Variant{lanes, kernel, 0};
+        if (l.v[i].lanes == lanes && l.v[i].kind == kind) return;
+    if (l.count < kMaxVariants) l.v[l.count++] = Variant{lanes, kernel, kind};
 }
 
 // Default thread-to-system mapping per n before any autotuning: one thread
 // per system while the matrix fits in registers without spilling, then the
 // fewest lanes per system that keep a lane's rows in registers.
-int default_lanes(int n)
+int default_register_lanes(int n)
 {
     if (n <= 9) return 1;
     if (n <= 12) return 2;
@@ -44,11 +45,19 @@ int default_lanes(int n)
     return 16;
 }
 
-const Variant *find_variant(int n, int layout, int op, int lanes)
+// Default variant id per n before any autotuning.
+int default_lanes(int n) { return variant_id(default_register_lanes(n), 0); }
+
+// Variant by id (lanes + 100 * kind); falls back to the register kernel of
+// the default lane count, then to anything registered.
+const Variant *find_variant(int n, int layout, int op, int id)
 {
     const VariantList &l = g_registry[n][layout][op];
     for (int i = 0; i < l.count; ++i)
-        if (l.v[i].lanes == lanes) return &l.v[i];
+        if (variant_id(l.v[i].lanes, l.v[i].kind) == id) return &l.v[i];
+    const int dflt = default_register_lanes(n);
+    for (int i = 0; i < l.count; ++i)
+        if (l.v[i].kind == 0 && l.v[i].lanes == dflt) return &l.v[i];
     return l.count ? &l.v[0] : nullptr;
 }
 
@@ -64,14 +73,15 @@ tl_status fail_cuda(tl_handle *h, cudaError_t e)
     return TL_ERR_CUDA;
 }
 
-// Resident blocks per SM of `kernel` at `block` threads (cached).
-static int blocks_per_sm(tl_handle *h, const void *kernel, int block)
+// Resident blocks per SM of `kernel` at `block` threads and `smem` bytes of
+// dynamic shared memory (cached).
+static int blocks_per_sm(tl_handle *h, const void *kernel, int block, size_t smem)
 {
-    auto key = std::make_pair(kernel, block);
+    auto key = std::make_pair(kernel, block * 1048576 + static_cast<int>(smem / 16));
     auto it = h->occupancy.find(key);
     if (it != h->occupancy.end()) return it->second;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, smem) != cudaSuccess) {
         cudaGetLastError();
         nb = 0;
     }
@@ -80,14 +90,18 @@ static int blocks_per_sm(tl_handle *h, const void *kernel, int block)
 }
 
 // Block size maximizing O + W: O the theoretical occupancy, W the mean fill
-// of the waves the grid needs.
-int pick_block(tl_handle *h, const void *kernel, int64_t threads)
+// of the waves the grid needs.  For shared-memory kernels (smem_per_lane_group
+// > 0) a block of b threads holds b / lanes systems.
+int pick_block(tl_handle *h, const void *kernel, int64_t threads, int lanes, size_t smem_per_system, int smem_limit)
 {
     static const int cands[] = {32, 64, 128};
-    int best = 128;
+    int best = 0;
     double best_score = -1.0;
     for (int b : cands) {
-        int nb = blocks_per_sm(h, kernel, b);
+        if (b < lanes) continue;
+        const size_t smem = smem_per_system ? (b / lanes) * smem_per_system : 0;
+        if (smem > static_cast<size_t>(smem_limit)) continue;
+        int nb = blocks_per_sm(h, kernel, b, smem);
         if (nb <= 0) continue;
         double O = static_cast<double>(nb) * b / h->max_threads_per_sm;
         int64_t blocks = (threads + b - 1) / b;
@@ -100,18 +114,46 @@ int pick_block(tl_handle *h, const void *kernel, int64_t threads)
             best = b;
         }
     }
+    if (best == 0) best = lanes > 32 ? lanes : 32;  // nothing resident: smallest block
     return best;
 }
 
-tl_status launch_variant(tl_handle *h, const Variant *v, int block, SolveArgs &args, cudaStream_t stream)
+tl_status launch_variant(tl_handle *h, const Variant *v, int n, int block, SolveArgs &args, cudaStream_t stream)
 {
     if (args.batch == 0) return TL_OK;
     const int64_t threads = args.batch * v->lanes;
-    if (block <= 0) block = pick_block(h, v->kernel, threads);
+    const size_t per_sys = v->kind == 1 ? smem_sys_bytes(n) : 0;
+    cudaError_t e;
+    int dyn_limit = h->max_smem_per_block;
+    if (v->kind == 1) {
+        auto it = h->smem_opt_in.find(v->kernel);
+        if (it == h->smem_opt_in.end()) {
+            // allow all the opt-in shared memory the static part leaves free,
+            // before any occupancy query
+            cudaFuncAttributes fa;
+            e = cudaFuncGetAttributes(&fa, v->kernel);
+            if (e != cudaSuccess) return fail_cuda(h, e);
+            dyn_limit = h->max_smem_per_block - static_cast<int>(fa.sharedSizeBytes);
+            e = cudaFuncSetAttribute(v->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_limit);
+            if (e != cudaSuccess) return fail_cuda(h, e);
+            h->smem_opt_in[v->kernel] = dyn_limit;
+        } else {
+            dyn_limit = it->second;
+        }
+    }
+    if (block <= 0) block = pick_block(h, v->kernel, threads, v->lanes, per_sys, dyn_limit);
     const int64_t grid = (threads + block - 1) / block;
     if (grid > INT_MAX) return TL_ERR_UNSUPPORTED;
-    void *params[] = {&args};
-    cudaError_t e = cudaLaunchKernel(v->kernel, dim3(static_cast<unsigned>(grid)), dim3(block), params, 0, stream);
+    if (v->kind == 1) {
+        const size_t smem = (block / v->lanes) * per_sys;
+        if (smem > static_cast<size_t>(dyn_limit)) return TL_ERR_UNSUPPORTED;
+        int nn = n;
+        void *params[] = {&args, &nn};
+        e = cudaLaunchKernel(v->kernel, dim3(static_cast<unsigned>(grid)), dim3(block), params, smem, stream);
+    } else {
+        void *params[] = {&args};
+        e = cudaLaunchKernel(v->kernel, dim3(static_cast<unsigned>(grid)), dim3(block), params, 0, stream);
+    }
     if (e != cudaSuccess) return fail_cuda(h, e);
     return TL_OK;
 }
@@ -121,7 +163,7 @@ tl_status launch_op(tl_handle *h, int n, int layout, int op, SolveArgs &args, cu
     const Choice &c = h->choice[n][layout][op];
     const Variant *v = find_variant(n, layout, op, c.lanes ? c.lanes : default_lanes(n));
     if (!v) return TL_ERR_UNSUPPORTED;
-    return launch_variant(h, v, c.block, args, stream);
+    return launch_variant(h, v, n, c.block, args, stream);
 }
 
 static bool misaligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) != 0; }
@@ -142,6 +184,8 @@ tl_status tl_create(tl_handle **out)
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&h->max_threads_per_sm, cudaDevAttrMaxThreadsPerMultiProcessor, h->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&h->max_smem_per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
     if (e != cudaSuccess) {
         delete h;
         return TL_ERR_CUDA;

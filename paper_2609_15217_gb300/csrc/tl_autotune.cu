@@ -1,0 +1,183 @@
+// tl_autotune.cu -- the size-aware dispatcher of the C ABI: per n, which
+// kernel variant (thread-to-system mapping and storage) and block size each
+// operation launches.  The paper reports "best X" curves where a run-time
+// dispatcher picks, at each problem size, the fastest specialization of a
+// solver family (Sec. 4.1, reporting convention); tl_autotune builds that
+// table by timing every registered variant on the current device, and
+// tl_dispatch_set / tl_dispatch_get read and write it directly.
+#include <cstdio>
+#include <vector>
+
+#include "tinylu.h"
+#include "tl_handle.h"
+#include "tl_internal.h"
+#include "tl_smem.cuh"
+
+namespace tl {
+namespace {
+
+// Uniform [-1, 1) numbers from a 64-bit counter hash (splitmix64 finalizer),
+// so the tuning batch needs no host data.
+__global__ void k_fill_uniform(double *p, int64_t count, uint64_t seed)
+{
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        uint64_t z = seed + static_cast<uint64_t>(i) * 0x9e3779b97f4a7c15ULL;
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+        z ^= z >> 31;
+        p[i] = static_cast<double>(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    }
+}
+
+bool op_takes_variant(int op) { return op == kOpGesv || op == kOpGesvLU || op == kOpGetrf; }
+
+}  // namespace
+}  // namespace tl
+
+using namespace tl;
+
+extern "C" tl_status tl_dispatch_set(tl_handle *h, int n, tl_layout layout, int variant, int block)
+{
+    if (!h) return TL_ERR_INVALID_ARG;
+    h->last_bad_arg = 0;
+    if (n < 1 || n > TL_MAX_N) return fail_arg(h, 2);
+    if (layout != TL_LAYOUT_PER_SYSTEM && layout != TL_LAYOUT_INTERLEAVED) return fail_arg(h, 3);
+    if (block != 0 && block != 32 && block != 64 && block != 128) return fail_arg(h, 5);
+    if (variant == 0) {
+        for (int op = 0; op < kOps; ++op) h->choice[n][layout][op] = Choice{0, 0};
+        return TL_OK;
+    }
+    bool found = false;
+    const VariantList &l = registry(n, layout, kOpGesv);
+    for (int i = 0; i < l.count; ++i)
+        if (variant_id(l.v[i].lanes, l.v[i].kind) == variant) found = true;
+    if (!found) return fail_arg(h, 4);
+    for (int op = 0; op < kOps; ++op)
+        if (op_takes_variant(op)) h->choice[n][layout][op] = Choice{variant, block};
+    // getrs and the ragged kernels only exist as register kernels: take the
+    // register variant with the same lane count when there is one
+    const int lanes = variant % 100;
+    for (int op : {static_cast<int>(kOpGetrs), static_cast<int>(kOpRagged)}) {
+        const VariantList &lo = registry(n, layout, op);
+        for (int i = 0; i < lo.count; ++i)
+            if (lo.v[i].kind == 0 && lo.v[i].lanes == lanes) h->choice[n][layout][op] = Choice{lanes, 0};
+    }
+    return TL_OK;
+}
+
+extern "C" tl_status tl_dispatch_get(tl_handle *h, int n, tl_layout layout, int *variant, int *block)
+{
+    if (!h) return TL_ERR_INVALID_ARG;
+    h->last_bad_arg = 0;
+    if (n < 1 || n > TL_MAX_N) return fail_arg(h, 2);
+    if (layout != TL_LAYOUT_PER_SYSTEM && layout != TL_LAYOUT_INTERLEAVED) return fail_arg(h, 3);
+    if (!variant) return fail_arg(h, 4);
+    const Choice &c = h->choice[n][layout][kOpGesv];
+    const Variant *v = find_variant(n, layout, kOpGesv, c.lanes ? c.lanes : default_lanes(n));
+    *variant = v ? variant_id(v->lanes, v->kind) : 0;
+    if (block) *block = c.block;
+    return TL_OK;
+}
+
+extern "C" tl_status tl_autotune(tl_handle *h, int n_min, int n_max, tl_layout layout, const char *table_path)
+{
+    if (!h) return TL_ERR_INVALID_ARG;
+    h->last_bad_arg = 0;
+    if (n_min < 1 || n_min > TL_MAX_N) return fail_arg(h, 2);
+    if (n_max < n_min || n_max > TL_MAX_N) return fail_arg(h, 3);
+    if (layout != TL_LAYOUT_PER_SYSTEM && layout != TL_LAYOUT_INTERLEAVED) return fail_arg(h, 4);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(nullptr, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+        return TL_ERR_UNSUPPORTED;
+    cudaGetLastError();
+
+    // One tuning batch sized for the largest n: enough systems to fill every
+    // SM several times over with the widest mapping.
+    const int64_t batch = static_cast<int64_t>(h->sm_count) * 512;
+    const int64_t ld = (batch + 31) / 32 * 32;
+    const int64_t nA = static_cast<int64_t>(n_max) * n_max * ld;
+    const int64_t nv = static_cast<int64_t>(n_max) * ld;
+    double *dA = nullptr, *db = nullptr, *dx = nullptr;
+    int32_t *dp = nullptr, *di = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    tl_status st = TL_OK;
+    struct Row {
+        int n, variant, block;
+        float ms;
+    };
+    std::vector<Row> table;
+    auto cleanup = [&]() {
+        cudaFree(dA);
+        cudaFree(db);
+        cudaFree(dx);
+        cudaFree(dp);
+        cudaFree(di);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    if (cudaMalloc(&dA, nA * sizeof(double)) != cudaSuccess || cudaMalloc(&db, nv * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&dx, nv * sizeof(double)) != cudaSuccess || cudaMalloc(&dp, nv * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&di, batch * sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return TL_ERR_NO_MEMORY;
+    }
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k_fill_uniform<<<h->sm_count * 4, 256>>>(dA, nA, 12345);
+    k_fill_uniform<<<h->sm_count * 4, 256>>>(db, nv, 54321);
+
+    for (int n = n_min; n <= n_max && st == TL_OK; ++n) {
+        SolveArgs args{dA, nullptr, db, dx, dp, di, ld, batch, 1};
+        const VariantList &l = registry(n, layout, kOpGesv);
+        float best_ms = 1e30f;
+        int best_var = 0, best_block = 0;
+        for (int i = 0; i < l.count && st == TL_OK; ++i) {
+            const Variant *v = &l.v[i];
+            for (int block : {32, 64, 128}) {
+                if (block < v->lanes) continue;
+                if (v->kind == 1 && (block / v->lanes) * smem_sys_bytes(n) + 1024 > static_cast<size_t>(h->max_smem_per_block))
+                    continue;
+                float ms_best = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    cudaEventRecord(e0, nullptr);
+                    st = launch_variant(h, v, n, block, args, nullptr);
+                    cudaEventRecord(e1, nullptr);
+                    if (st != TL_OK) break;
+                    if (cudaEventSynchronize(e1) != cudaSuccess) {
+                        st = fail_cuda(h, cudaGetLastError());
+                        break;
+                    }
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0 && ms < ms_best) ms_best = ms;  // first run warms up
+                }
+                if (st != TL_OK) break;
+                if (ms_best < best_ms) {
+                    best_ms = ms_best;
+                    best_var = variant_id(v->lanes, v->kind);
+                    best_block = block;
+                }
+            }
+        }
+        if (st == TL_OK && best_var) {
+            tl_dispatch_set(h, n, layout, best_var, best_block);
+            table.push_back(Row{n, best_var, best_block, best_ms});
+        }
+    }
+    cleanup();
+    if (st == TL_OK && table_path) {
+        FILE *f = std::fopen(table_path, "w");
+        if (!f) return TL_ERR_INVALID_ARG;
+        std::fprintf(f, "{\"layout\": %d, \"batch\": %lld, \"entries\": [", static_cast<int>(layout),
+                     static_cast<long long>(batch));
+        for (size_t i = 0; i < table.size(); ++i)
+            std::fprintf(f, "%s{\"n\": %d, \"variant\": %d, \"lanes\": %d, \"storage\": \"%s\", \"block\": %d, \"ms\": %.6f}",
+                         i ? ", " : "", table[i].n, table[i].variant, table[i].variant % 100,
+                         table[i].variant >= 100 ? "shared" : "registers", table[i].block, table[i].ms);
+        std::fprintf(f, "]}\n");
+        std::fclose(f);
+    }
+    return st;
+}

@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <functional>
 #include <unordered_map>
+#include <unordered_set>
 #include <utility>
 
 #include "tinylu.h"
@@ -26,11 +27,13 @@ struct PairHash {
 };
 
 int default_lanes(int n);
-const Variant *find_variant(int n, int layout, int op, int lanes);
+int default_register_lanes(int n);
+const Variant *find_variant(int n, int layout, int op, int id);
 tl_status fail_arg(tl_handle *h, int pos);
 tl_status fail_cuda(tl_handle *h, cudaError_t e);
-int pick_block(tl_handle *h, const void *kernel, int64_t threads);
-tl_status launch_variant(tl_handle *h, const Variant *v, int block, SolveArgs &args, cudaStream_t stream);
+int pick_block(tl_handle *h, const void *kernel, int64_t threads, int lanes, size_t smem_per_system,
+               int smem_limit);
+tl_status launch_variant(tl_handle *h, const Variant *v, int n, int block, SolveArgs &args, cudaStream_t stream);
 tl_status launch_op(tl_handle *h, int n, int layout, int op, SolveArgs &args, cudaStream_t stream);
 tl_status ensure_workspace(tl_handle *h, size_t bytes, cudaStream_t stream);
 // Buckets `batch` systems by n[s] using the int32 scratch `ws` (3*64 bin
@@ -44,10 +47,12 @@ struct tl_handle {
     int device = 0;
     int sm_count = 1;
     int max_threads_per_sm = 2048;
+    int max_smem_per_block = 48 * 1024;
     int last_cuda_error = 0;
     int last_bad_arg = 0;
     tl::Choice choice[TL_MAX_N + 1][2][tl::kOps] = {};
     std::unordered_map<std::pair<const void *, int>, int, tl::PairHash> occupancy;
+    std::unordered_map<const void *, int> smem_opt_in;  // kernel -> dynamic smem limit set
     // device workspace owned by the handle (grown on demand, never inside a
     // stream capture) and pinned host staging buffers
     void *ws = nullptr;

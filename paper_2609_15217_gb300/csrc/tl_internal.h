@@ -43,21 +43,26 @@ struct RaggedArgs {
 
 // Kernel variant for one (n, layout, operation): how many lanes share a
 // system (1 = one thread per system) and the launch entry.
+//   kind 0: register kernel compiled for one n, kernel(SolveArgs)
+//   kind 1: shared-memory kernel for any n, kernel(SolveArgs, int n) with
+//           smem_sys_bytes(n) of dynamic shared memory per system
+// The variant id is lanes + 100 * kind.
 struct Variant {
     int lanes;                     // T
     const void *kernel;            // __global__ function, for occupancy queries
-    int regs_hint;                 // 0 when unknown
+    int kind;
 };
+__host__ __device__ constexpr int variant_id(int lanes, int kind) { return lanes + 100 * kind; }
 
 // Registry filled by the instantiation units (tl_inst.cu, one per (N, T)).
 enum : int { kOpGesv = 0, kOpGesvLU = 1, kOpGetrf = 2, kOpGetrs = 3, kOpRagged = 4 };
 constexpr int kOps = 5;
-constexpr int kMaxVariants = 6;
+constexpr int kMaxVariants = 8;
 struct VariantList {
     int count;
     Variant v[kMaxVariants];
 };
 VariantList &registry(int n, int layout, int op);
-void register_variant(int n, int layout, int op, int lanes, const void *kernel);
+void register_variant(int n, int layout, int op, int lanes, const void *kernel, int kind = 0);
 
 }  // namespace tl

@@ -121,6 +121,7 @@ tl_status ragged_solve(tl_handle *h, int64_t batch, const int32_t *n, RaggedArgs
     for (int nn = 1; nn <= TL_MAX_N; ++nn) {
         const Choice &c = h->choice[nn][kPerSystem][kOpRagged];
         const Variant *v = find_variant(nn, kPerSystem, kOpRagged, c.lanes ? c.lanes : default_lanes(nn));
+        // (ragged launches use the register kernels only)
         if (!v) return TL_ERR_UNSUPPORTED;
         const int blk = 128;
         int nb = 0;

@@ -48,6 +48,8 @@ _SIGS = {
     "tl_lupp_solve_batched_noalloc": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _int),
     "tl_newton_integrate": ([_vp, C.POINTER(tl_law), _i64, _vp, _vp, _vp, _vp, _vp, C.c_double, _int, _vp], _int),
     "tl_autotune": ([_vp, _int, _int, _int, C.c_char_p], _int),
+    "tl_dispatch_set": ([_vp, _int, _int, _int, _int], _int),
+    "tl_dispatch_get": ([_vp, _int, _int, C.POINTER(_int), C.POINTER(_int)], _int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -169,6 +171,23 @@ def tl_newton_integrate(h, law, npoints, inputs, x, outputs, iterations, status,
 
 def tl_autotune(h, n_min, n_max, layout, table_path=None):
     return _lib.tl_autotune(h, n_min, n_max, layout, table_path.encode() if table_path else None)
+
+
+def tl_dispatch_set(h, n, layout, variant, block=0):
+    return _lib.tl_dispatch_set(h, n, layout, variant, block)
+
+
+def tl_dispatch_get(h, n, layout):
+    """Returns (status, variant, block)."""
+    v, b = C.c_int(0), C.c_int(0)
+    st = _lib.tl_dispatch_get(h, n, layout, C.byref(v), C.byref(b))
+    return st, v.value, b.value
+
+
+def variant_id(lanes, shared=False):
+    """Dispatch id of a kernel variant: lanes per system + 100 for the
+    shared-memory storage."""
+    return lanes + (100 if shared else 0)
 
 
 def library():
