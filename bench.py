@@ -37,6 +37,22 @@ NEWTON_POINTS = 1 << 22
 _T0 = time.perf_counter()
 
 
+def rank_seed(base, rank):
+    """Per-rank seed: every rank solves its own independent batch (weak
+    scaling, no data exchanged)."""
+    return base + 100 * rank
+
+
+def max_over_ranks(value, dist, device=None):
+    """Step time of the job = the slowest rank's (max over ranks)."""
+    if dist is None or not dist.is_initialized():
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def log(msg):
     sys.stderr.write(f"[bench {time.perf_counter() - _T0:8.1f}s] {msg}\n")
     sys.stderr.flush()
@@ -385,6 +401,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-newton", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--batch", type=int, default=None,
                     help="cap on systems per n (small cases for profiling; the default is the full sweep)")
     ap.add_argument("--ref-seconds-per-n", type=float, default=0.3)
@@ -414,8 +431,19 @@ def main():
 
     h = tl.tl_create()
     n_list = list(range(args.nmin, args.nmax + 1))
+    tune = {}
+    if not args.no_autotune:
+        # size-aware dispatcher: time every kernel variant per n once, before
+        # anything is timed (the "best X" selection of the paper's Sec. 4.1)
+        log("autotune")
+        for layout in (1, 0):
+            path = os.path.join(ROOT, f"_build/autotune_layout{layout}.json")
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            tl.check("tl_autotune", tl.tl_autotune(h, args.nmin, args.nmax, layout, path), h)
+            with open(path) as f:
+                tune[layout] = {e["n"]: e["variant"] for e in json.load(f)["entries"]}
     t_gen = time.perf_counter()
-    data = make_sweep(n_list, 1, 1236 + 100 * rank, device, torch, L, I, args.batch)
+    data = make_sweep(n_list, 1, rank_seed(1236, rank), device, torch, L, I, args.batch)
     gen_s = time.perf_counter() - t_gen
 
     log("timing interleaved sweep")
@@ -423,11 +451,7 @@ def main():
         step_ms, per_n = time_sweep(tl, h, data, 1, args.steps, args.warmup, torch, barrier)
     clocks = clk.summary()
 
-    med_step = statistics.median(step_ms)
-    if dist is not None:
-        t = torch.tensor([med_step], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        med_step = float(t.item())
+    med_step = max_over_ranks(statistics.median(step_ms), dist, device)
     systems_rank = sum(d["S"] for d in data.values())
     value = systems_rank * world / (med_step / 1e3)
 
@@ -461,7 +485,7 @@ def main():
     extra = {}
     if not args.no_per_system:
         log("per-system layout sweep")
-        data_ps = make_sweep(n_list, 0, 1236 + 100 * rank, device, torch, L, I, args.batch)
+        data_ps = make_sweep(n_list, 0, rank_seed(1236, rank), device, torch, L, I, args.batch)
         ms_ps, per_n_ps = time_sweep(tl, h, data_ps, 0, max(2, args.steps // 2), 1, torch, barrier)
         sys_ps = sum(d["S"] for d in data_ps.values())
         extra["per_system_layout"] = {
@@ -473,7 +497,7 @@ def main():
 
     if not args.no_newton:
         log("newton")
-        extra["newton"] = newton_bench(tl, h, max(2, args.steps // 2), 2, torch, device, I, 1237 + 100 * rank)
+        extra["newton"] = newton_bench(tl, h, max(2, args.steps // 2), 2, torch, device, I, rank_seed(1237, rank))
         extra["newton"]["points_per_s"] *= world
         torch.cuda.empty_cache()
 
@@ -508,7 +532,7 @@ def main():
                        f"{sum(bytes_per_system(n) * sweep_batch(n) for n in n_list) / 1e9:.1f} GB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks, "per_n": per_n_out, "gen_s": gen_s, **extra,
+            "clocks": clocks, "per_n": per_n_out, "gen_s": gen_s, "dispatch": tune, **extra,
         }
         print(json.dumps(out))
     if dist is not None:
