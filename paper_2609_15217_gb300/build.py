@@ -21,7 +21,7 @@ LIB = os.path.join(PKG, "libtinylu.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-              "-I" + INCLUDE, "-I" + CSRC]
+              "-I" + INCLUDE, "-I" + CSRC] + os.environ.get("TL_NVCC_FLAGS", "").split()
 
 # (n, lanes per system) kernel families compiled into the library.
 #   lanes = 1: one thread per system, matrix in registers (n <= 9)

@@ -24,13 +24,13 @@ static VariantList g_registry[TL_MAX_N + 1][2][kOps];
 
 VariantList &registry(int n, int layout, int op) { return g_registry[n][layout][op]; }
 
-void register_variant(int n, int layout, int op, int lanes, const void *kernel, int kind)
+void register_variant(int n, int layout, int op, int lanes, const void *kernel, int kind, const void *fixup)
 {
     if (n < 1 || n > TL_MAX_N || layout < 0 || layout > 1 || op < 0 || op >= kOps) return;
     VariantList &l = g_registry[n][layout][op];
     for (int i = 0; i < l.count; ++i)
         if (l.v[i].lanes == lanes && l.v[i].kind == kind) return;
-    if (l.count < kMaxVariants) l.v[l.count++] = Variant{lanes, kernel, kind};
+    if (l.count < kMaxVariants) l.v[l.count++] = Variant{lanes, kernel, kind, fixup};
 }
 
 // Default thread-to-system mapping per n before any autotuning: one thread
@@ -122,7 +122,7 @@ tl_status launch_variant(tl_handle *h, const Variant *v, int n, int block, Solve
 {
     if (args.batch == 0) return TL_OK;
     const int64_t threads = args.batch * v->lanes;
-    const size_t per_sys = v->kind == 1 ? smem_sys_bytes(n) : 0;
+    const size_t per_sys = v->kind == 1 ? smem_sys_bytes(n, v->lanes) : 0;
     cudaError_t e;
     int dyn_limit = h->max_smem_per_block;
     if (v->kind == 1) {
@@ -153,6 +153,10 @@ tl_status launch_variant(tl_handle *h, const Variant *v, int n, int block, Solve
     } else {
         void *params[] = {&args};
         e = cudaLaunchKernel(v->kernel, dim3(static_cast<unsigned>(grid)), dim3(block), params, 0, stream);
+        if (e == cudaSuccess && v->fixup) {
+            const int64_t fgrid = (args.batch + 127) / 128;
+            e = cudaLaunchKernel(v->fixup, dim3(static_cast<unsigned>(fgrid)), dim3(128), params, 0, stream);
+        }
     }
     if (e != cudaSuccess) return fail_cuda(h, e);
     return TL_OK;

@@ -31,6 +31,16 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+// Reciprocal of the one-thread fast path: the FP64 instruction (0) or the
+// integer-pipe sequence (1).
+#ifndef TL_THREAD_RCP_INT
+#define TL_THREAD_RCP_INT 0
+#endif
+// Reciprocal of the sub-warp group solvers (same choice).
+#ifndef TL_GROUP_RCP_INT
+#define TL_GROUP_RCP_INT 0
+#endif
+
 namespace tl {
 namespace dev {
 
@@ -69,6 +79,107 @@ __device__ __forceinline__ double neg(double x)
         : "=d"(r)
         : "d"(x));
     return r;
+}
+
+// RN(1/a), IEEE binary64 round to nearest even, computed with integer and
+// FP32 instructions only, so the reciprocal of every elimination step costs
+// no FP64 pipe time (the FP64 pipe is the bottleneck; the integer pipes are
+// mostly idle).  Method: a = X * 2^(e-1075) with the 53-bit integer
+// significand X; the result significand is Q = RN(2^105 / X):
+//   1. seed  Y0 = RN32(1 / (X >> 29)) * 2^76         (~22 correct bits)
+//   2. two Newton steps in fixed point, Y += Y * (2^105 - X Y) / 2^105
+//      (the first with a 128-bit residual, the second with its exact low
+//      64 bits)                                       (Y within +-2 of 2^105/X)
+//   3. exact remainder R = 2^105 - X Y (low 64 bits of the product), Y
+//      adjusted until 0 <= R < X, then Y += (2R > X)   (2R == X is impossible
+//      for X > 2^52: 2^106 / X would have to be an odd integer).
+// A power-of-two significand gives Y = 2^53, which the final packing carries
+// into the exponent.  Inputs whose reciprocal would be subnormal or that are
+// zero, subnormal, Inf or NaN take __drcp_rn, behind a warp-uniform branch so
+// that the common path issues no FP64 instruction at all.
+// Integer-pipe core of RN(1/a): exact for normal |a| in [DBL_MIN, 2^1021)
+// (biased exponent 1..2044); any other input returns an unspecified value.
+// Straight-line code without a branch, so the compiler can interleave it
+// with independent FMAs.
+__device__ __forceinline__ double rcp_rn_fast(double a)
+{
+    unsigned long long bits;
+    asm("mov.b64 %0, %1;" : "=l"(bits) : "d"(a));  // opaque: no FP pattern matching
+    const int eb = static_cast<int>((bits >> 52) & 0x7ff);
+    const unsigned long long sign = bits & 0x8000000000000000ULL;
+    const unsigned long long X = (bits & 0x000fffffffffffffULL) | 0x0010000000000000ULL;
+    // 1. seed from the FP32 reciprocal of the top 24 bits (exact as a float)
+    const unsigned xh = static_cast<unsigned>(X >> 29);
+    const float xf = __uint_as_float((150u << 23) | (xh & 0x7fffffu));
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(xf));
+    const unsigned rb = __float_as_uint(rf);
+    unsigned long long Y = static_cast<unsigned long long>((rb & 0x7fffffu) | 0x800000u) << ((rb >> 23) - 74);
+    // 2a. D = 2^105 - X Y as a 128-bit value, |D| < 2^84; Y += Y D / 2^105
+    {
+        const unsigned long long plo = X * Y;
+        const unsigned long long phi = __umul64hi(X, Y);
+        const unsigned long long dlo = 0ULL - plo;
+        const unsigned long long dhi = (1ULL << 41) - phi - (plo != 0ULL ? 1ULL : 0ULL);
+        const long long dsh = static_cast<long long>((dhi << 24) | (dlo >> 40));  // D >> 40
+        Y = static_cast<unsigned long long>(static_cast<long long>(Y) + (__mul64hi(static_cast<long long>(Y), dsh) >> 1));
+    }
+    // 2b. |D| < 2^63 now: its low 64 bits are exact
+    {
+        const long long d1 = static_cast<long long>(0ULL - X * Y);
+        Y = static_cast<unsigned long long>(static_cast<long long>(Y) + (__mul64hi(static_cast<long long>(Y), d1) >> 41));
+    }
+    // 3. exact remainder and rounding
+    long long R = static_cast<long long>(0ULL - X * Y);
+    const long long Xs = static_cast<long long>(X);
+#pragma unroll
+    for (int it = 0; it < 3; ++it) {
+        const bool lo = R < 0;
+        Y = lo ? Y - 1 : Y;
+        R = lo ? R + Xs : R;
+    }
+#pragma unroll
+    for (int it = 0; it < 3; ++it) {
+        const bool hi = R >= Xs;
+        Y = hi ? Y + 1 : Y;
+        R = hi ? R - Xs : R;
+    }
+    Y += (2 * R > Xs) ? 1ULL : 0ULL;
+    // a power-of-two significand gives Y = 2^53, carried into the exponent
+    return __longlong_as_double(static_cast<long long>(sign | ((static_cast<unsigned long long>(2045 - eb) << 52) +
+                                                               (Y - 0x0010000000000000ULL))));
+}
+
+// True when rcp_rn_fast is exact for a value of magnitude bits m.
+__device__ __forceinline__ bool rcp_fast_ok(unsigned long long m)
+{
+    return m >= 0x0010000000000000ULL && m < 0x7fd0000000000000ULL;
+}
+
+// Out-of-line so that the compiler cannot if-convert the rare fallback into
+// predicated FP64 instructions that every call would then issue.
+static __device__ __noinline__ double rcp_rn_fallback(double a) { return __drcp_rn(a); }
+
+// RN(1/a) for every input (IEEE binary64, round to nearest even):
+// rcp_rn_fast where it is exact, __drcp_rn otherwise behind a warp-uniform
+// branch.  The method of rcp_rn_fast: a = X * 2^(e-1075) with the 53-bit
+// integer significand X; the result significand is Q = RN(2^105 / X):
+//   1. seed  Y0 = RN32(1 / (X >> 29)) * 2^76         (~22 correct bits)
+//   2. two Newton steps in fixed point, Y += Y * (2^105 - X Y) / 2^105
+//      (the first with a 128-bit residual, the second with its exact low
+//      64 bits)                                       (Y within +-2 of 2^105/X)
+//   3. exact remainder R = 2^105 - X Y (low 64 bits of the product), Y
+//      adjusted until 0 <= R < X, then Y += (2R > X)   (2R == X is impossible
+//      for X > 2^52: 2^106 / X would have to be an odd integer).
+__device__ __forceinline__ double rcp_rn(double a)
+{
+    const unsigned long long m = mag_bits(a);
+    double res = rcp_rn_fast(a);
+    const bool special = !rcp_fast_ok(m);
+    if (__any_sync(__activemask(), special)) {
+        if (special) res = rcp_rn_fallback(a);
+    }
+    return res;
 }
 
 // 64-bit select done on the integer pipe (two 32-bit selects).
@@ -110,30 +221,148 @@ template <int N, bool KEEP_L, int NB>
 __device__ __forceinline__ int lu_thread_factor(double (&a)[N][N], double (&b)[NB > 0 ? NB : 1][N],
                                                 int (&piv)[N], double (&rcp)[N], bool &tiny)
 {
+    // Look-ahead: step k updates column k+1 first, then searches its pivot
+    // and forms the next reciprocal, and only then updates the remaining
+    // columns, so the integer search and reciprocal of step k+1 overlap the
+    // FMAs of step k.  Every element still receives its updates in
+    // increasing k, so the rounding sequence is unchanged.
     int info = 0;
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-        // a2: pivot search on the magnitude bit patterns (first maximum).
-        unsigned long long best = mag_bits(a[k][k]);
-        int p = k;
+    // pivot search of column k (first maximum of the magnitude bits)
+    auto search = [&](int k, int &p, unsigned long long &best, double &pv) {
+        best = mag_bits(a[k][k]);
+        p = k;
+        pv = a[k][k];
 #pragma unroll
         for (int i = k + 1; i < N; ++i) {
-            unsigned long long m = mag_bits(a[i][k]);
-            bool gt = m > best;
+            const unsigned long long m = mag_bits(a[i][k]);
+            const bool gt = m > best;
             best = gt ? m : best;
             p = gt ? i : p;
+            pv = sel(gt, a[i][k], pv);
         }
+    };
+    int p_next;
+    unsigned long long best_next;
+    double pv_next;
+    search(0, p_next, best_next, pv_next);
+    double r_next = rcp_rn(pv_next);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const int p = p_next;
+        const unsigned long long best = best_next;
+        const double pv = pv_next;
+        const double r = r_next;
         piv[k] = p;
         rcp[k] = 0.0;
-        if (best == 0ULL) {
+        const bool zero = (best == 0ULL);
+        if (zero) {
             if (info == 0) info = k + 1;
             // the column below is zero; store it in the negated convention
             // too so that the final sign flip restores it bit for bit
 #pragma unroll
             for (int i = k + 1; i < N; ++i) a[i][k] = neg(a[i][k]);
-            continue;
+        } else {
+            // a3: physical row interchange k <-> p as a register permutation.
+            const int j0 = KEEP_L ? 0 : k;
+#pragma unroll
+            for (int i = k + 1; i < N; ++i) {
+                const bool s = (p == i);
+#pragma unroll
+                for (int j = j0; j < N; ++j) {
+                    double t = a[k][j];
+                    a[k][j] = sel(s, a[i][j], t);
+                    a[i][j] = sel(s, t, a[i][j]);
+                }
+#pragma unroll
+                for (int c = 0; c < NB; ++c) {
+                    double t = b[c][k];
+                    b[c][k] = sel(s, b[c][i], t);
+                    b[c][i] = sel(s, t, b[c][i]);
+                }
+            }
+            // a4: multipliers, kept NEGATED: -l_ik = RN(a_ik * (-r)); the
+            // quotient path for |pivot| < DBL_MIN is a warp-uniform branch.
+            const bool small = best < kDblMinBits;
+            if (!__any_sync(__activemask(), small)) {
+                rcp[k] = r;
+                const double nr = neg(r);
+#pragma unroll
+                for (int i = k + 1; i < N; ++i) a[i][k] = __dmul_rn(a[i][k], nr);
+            } else {
+                rcp[k] = r;
+                const double nr = neg(r);
+                const double npv = neg(pv);
+                tiny = tiny || small;
+#pragma unroll
+                for (int i = k + 1; i < N; ++i)
+                    a[i][k] = small ? __ddiv_rn(a[i][k], npv) : __dmul_rn(a[i][k], nr);
+            }
+            // a5 part 1: column k+1 of the Schur update
+            if (k + 1 < N) {
+#pragma unroll
+                for (int i = k + 1; i < N; ++i) a[i][k + 1] = __fma_rn(a[i][k], a[k][k + 1], a[i][k + 1]);
+            }
         }
-        // a3: physical row interchange k <-> p as a register permutation.
+        // look-ahead: pivot and reciprocal of step k+1
+        if (k + 1 < N) {
+            search(k + 1, p_next, best_next, pv_next);
+            r_next = rcp_rn(pv_next);
+        }
+        if (!zero) {
+            // a5 part 2: the remaining columns; a6 (forward part): b follows
+            // as extra columns.
+#pragma unroll
+            for (int j = k + 2; j < N; ++j)
+#pragma unroll
+                for (int i = k + 1; i < N; ++i) a[i][j] = __fma_rn(a[i][k], a[k][j], a[i][j]);
+#pragma unroll
+            for (int c = 0; c < NB; ++c)
+#pragma unroll
+                for (int i = k + 1; i < N; ++i) b[c][i] = __fma_rn(a[i][k], b[c][k], b[c][i]);
+        }
+    }
+    return info;
+}
+
+// Branch-free fast path of lu_thread_factor for the common case: every
+// pivot normal and below 2^1021 in magnitude.  The same arithmetic, the same
+// look-ahead, no data-dependent branch at all (so the compiler can schedule
+// each step as one block), and the reciprocal entirely on the integer pipe.
+// Returns true when the system needs the exact general path instead (a zero,
+// subnormal, huge or non-finite pivot was met): the caller then restarts the
+// system from its input with lu_thread_factor.
+template <int N, bool KEEP_L, int NB>
+__device__ __forceinline__ bool lu_thread_factor_fast(double (&a)[N][N], double (&b)[NB > 0 ? NB : 1][N],
+                                                      int (&piv)[N], double (&rcp)[N])
+{
+    // The whole factorization is one straight-line block (every loop is
+    // unrolled and there is no data-dependent branch), so the instruction
+    // scheduler is free to overlap the integer pivot search and reciprocal
+    // of a step with the FMAs still in flight from the previous one.
+    bool slow = false;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        // a2: pivot search (first maximum of the magnitude bits)
+        unsigned long long best = mag_bits(a[k][k]);
+        int p = k;
+        double pv = a[k][k];
+#pragma unroll
+        for (int i = k + 1; i < N; ++i) {
+            const unsigned long long m = mag_bits(a[i][k]);
+            const bool gt = m > best;
+            best = gt ? m : best;
+            p = gt ? i : p;
+            pv = sel(gt, a[i][k], pv);
+        }
+        slow = slow || !rcp_fast_ok(best);
+        piv[k] = p;
+#if TL_THREAD_RCP_INT
+        const double r = rcp_rn_fast(pv);
+#else
+        const double r = __drcp_rn(pv);
+#endif
+        rcp[k] = r;
+        // a3: interchange as a register permutation
         const int j0 = KEEP_L ? 0 : k;
 #pragma unroll
         for (int i = k + 1; i < N; ++i) {
@@ -151,31 +380,10 @@ __device__ __forceinline__ int lu_thread_factor(double (&a)[N][N], double (&b)[N
                 b[c][i] = sel(s, t, b[c][i]);
             }
         }
-        // a4: multipliers with one correctly rounded reciprocal.  They are
-        // kept NEGATED, -l_ik = RN(a_ik * (-r)) (negation commutes with
-        // rounding), so the update below needs no negated operand.
-        // The quotient path for |pivot| < DBL_MIN is entered by a warp-uniform
-        // branch so that the common path never issues division code.
-        const double pv = a[k][k];
-        const bool small = best < kDblMinBits;
-        if (!__any_sync(__activemask(), small)) {
-            const double r = __drcp_rn(pv);
-            rcp[k] = r;
-            const double nr = neg(r);
+        // a4: negated multipliers; a5 + forward part of a6
+        const double nr = neg(r);
 #pragma unroll
-            for (int i = k + 1; i < N; ++i) a[i][k] = __dmul_rn(a[i][k], nr);
-        } else {
-            const double r = __drcp_rn(pv);
-            rcp[k] = r;
-            const double nr = neg(r);
-            const double npv = neg(pv);
-            tiny = tiny || small;
-#pragma unroll
-            for (int i = k + 1; i < N; ++i)
-                a[i][k] = small ? __ddiv_rn(a[i][k], npv) : __dmul_rn(a[i][k], nr);
-        }
-        // a5: rank-1 Schur update a_ij + (-l_ik) u_kj; a6 (forward part): b
-        // follows as extra columns.
+        for (int i = k + 1; i < N; ++i) a[i][k] = __dmul_rn(a[i][k], nr);
 #pragma unroll
         for (int j = k + 1; j < N; ++j)
 #pragma unroll
@@ -185,7 +393,23 @@ __device__ __forceinline__ int lu_thread_factor(double (&a)[N][N], double (&b)[N
 #pragma unroll
             for (int i = k + 1; i < N; ++i) b[c][i] = __fma_rn(a[i][k], b[c][k], b[c][i]);
     }
-    return info;
+    return slow;
+}
+
+// Back substitution of the fast path (all pivots normal): x_i = s * RN(1/u_ii).
+template <int N>
+__device__ __forceinline__ void lu_thread_backsolve_fast(const double (&a)[N][N], double (&y)[N],
+                                                         const double (&rcp)[N])
+{
+    double nx[N];
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {
+        double s = y[i];
+#pragma unroll
+        for (int j = N - 1; j > i; --j) s = __fma_rn(a[i][j], nx[j], s);
+        y[i] = __dmul_rn(s, rcp[i]);
+        nx[i] = neg(y[i]);
+    }
 }
 
 // lu_thread_factor leaves -l_ik below the diagonal; flip them back to the
@@ -260,7 +484,7 @@ __device__ __forceinline__ void lu_thread_forward(const double (&a)[N][N], const
 
 // Device-callable fused solve for one system held by the calling thread:
 // A (destroyed) x = b (overwritten by x).  Returns info; x is NaN on
-// info != 0.  This is the entry the fused Newton kernel calls.
+// info != 0.  The exact general path (zero, tiny, huge or non-finite pivots).
 template <int N>
 __device__ __forceinline__ int lupp_solve(double (&a)[N][N], double (&b)[N], int (&piv)[N])
 {
@@ -282,6 +506,20 @@ __device__ __forceinline__ int lupp_solve(double (&a)[N][N], double (&b)[N], int
         for (int i = 0; i < N; ++i) b[i] = nan_value();
     }
     return info;
+}
+
+// The fast solve: returns false when it cannot vouch for the result (the
+// system met a zero, tiny, huge or non-finite pivot or input); the caller must
+// then restore a and b and use lupp_solve.  Same arithmetic otherwise.
+template <int N>
+__device__ __forceinline__ bool lupp_solve_fast(double (&a)[N][N], double (&b)[N], int (&piv)[N])
+{
+    const bool bad = any_nonfinite<N>(a);
+    double rcp[N];
+    double (&bb)[1][N] = *reinterpret_cast<double (*)[1][N]>(&b);
+    const bool slow = lu_thread_factor_fast<N, false, 1>(a, bb, piv, rcp);
+    lu_thread_backsolve_fast<N>(a, b, rcp);
+    return !(slow || bad);
 }
 
 // ---------------------------------------------------------------------------
@@ -335,13 +573,11 @@ __device__ __forceinline__ int lu_group_factor(double (&a)[Group<N, T>::K][N],
 {
     constexpr int K = Group<N, T>::K;
     int info = 0;
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-        const int owner_k = k % T;   // lane (in group) holding row k
-        const int slot_k = k / T;
-        // a2: local candidate, then butterfly across the group.
-        double cv = 0.0;
-        int crow = N;  // sentinel: no candidate
+    // a2: this lane's candidate in column k, then the butterfly across the
+    // group (first maximum: ties go to the smaller row).
+    auto search = [&](int k, double &cv, int &crow) {
+        cv = 0.0;
+        crow = N;  // sentinel: no candidate
 #pragma unroll
         for (int s = 0; s < K; ++s) {
             if (s * T < N && (T - 1) + s * T >= k) {
@@ -354,15 +590,38 @@ __device__ __forceinline__ int lu_group_factor(double (&a)[Group<N, T>::K][N],
             }
         }
         group_argmax<T>(cv, crow);
-        const int p = crow;
+    };
+    // Look-ahead as in lu_thread_factor: column k+1 is updated first, the
+    // search and reciprocal of step k+1 are issued, then the other columns.
+    auto group_rcp = [](double v) {
+#if TL_GROUP_RCP_INT
+        return rcp_rn(v);
+#else
+        return __drcp_rn(v);
+#endif
+    };
+    double cv_next;
+    int crow_next;
+    search(0, cv_next, crow_next);
+    double r_next = group_rcp(cv_next);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const int owner_k = k % T;   // lane (in group) holding row k
+        const int slot_k = k / T;
+        const double cv = cv_next;
+        const int p = crow_next;
+        const double r = r_next;
         const bool zero = (mag_bits(cv) == 0ULL);
         if (t == owner_k) pivk[slot_k] = p;
         if (zero && info == 0) info = k + 1;
 
-        // a3: interchange rows k and p between their owning lanes.
+        // a3: interchange rows k and p between their owning lanes.  The
+        // shuffle that brings row p to row k reaches every lane of the
+        // group, so it is also the broadcast of the pivot row u_kj.
         const int owner_p = p % T;
         const int slot_p = p / T;
         const int j0 = KEEP_L ? 0 : k;
+        double uk[N + 1];
 #pragma unroll
         for (int j = j0; j < N + NB; ++j) {
             double vk, vp = 0.0;
@@ -377,6 +636,7 @@ __device__ __forceinline__ int lu_group_factor(double (&a)[Group<N, T>::K][N],
             }
             const double new_k = __shfl_sync(0xffffffffu, vp, lane0 + owner_p);
             const double new_p = __shfl_sync(0xffffffffu, vk, lane0 + owner_k);
+            if (j > k) uk[j] = new_k;
             if (j < N) {
 #pragma unroll
                 for (int s = 0; s < K; ++s)
@@ -389,14 +649,13 @@ __device__ __forceinline__ int lu_group_factor(double (&a)[Group<N, T>::K][N],
             }
         }
 
-        // a4: reciprocal of the pivot (the butterfly left its value in cv on
-        // every lane) and the multipliers of this lane's live rows.
+        // a4: reciprocal (formed by the look-ahead; the butterfly left the
+        // pivot value in cv on every lane) and this lane's multipliers, kept
+        // negated (see lu_thread_factor); a zero column is flipped as well so
+        // the final sign flip restores it bit for bit.
         const bool small = !zero && mag_bits(cv) < kDblMinBits;
-        const double r = __drcp_rn(cv);
         if (t == owner_k) rcp[slot_k] = r;
         tiny = tiny || small;
-        // multipliers kept negated (see lu_thread_factor); a zero column is
-        // flipped as well so the final sign flip restores it bit for bit
         const double nr = neg(r);
 #pragma unroll
         for (int s = 0; s < K; ++s) {
@@ -425,11 +684,20 @@ __device__ __forceinline__ int lu_group_factor(double (&a)[Group<N, T>::K][N],
                 }
             }
         }
-        // Broadcast of the pivot row u_kj (j > k) and y_k, then a5 update.
-        double uk[N + 1];
+        // a5 part 1: column k+1
+        if (k + 1 < N) {
 #pragma unroll
-        for (int j = k + 1; j < N; ++j) uk[j] = __shfl_sync(0xffffffffu, a[slot_k][j], lane0 + owner_k);
-        if (NB > 0) uk[N] = __shfl_sync(0xffffffffu, b[slot_k], lane0 + owner_k);
+            for (int s = 0; s < K; ++s) {
+                if (Group<N, T>::slot_alive(s, k)) {
+                    const int i = t + s * T;
+                    if (!zero && i > k && i < N) a[s][k + 1] = __fma_rn(a[s][k], uk[k + 1], a[s][k + 1]);
+                }
+            }
+            // look-ahead: pivot and reciprocal of step k+1
+            search(k + 1, cv_next, crow_next);
+            r_next = group_rcp(cv_next);
+        }
+        // a5 part 2: the other columns, and b (forward part of a6)
 #pragma unroll
         for (int s = 0; s < K; ++s) {
             if (Group<N, T>::slot_alive(s, k)) {
@@ -437,7 +705,7 @@ __device__ __forceinline__ int lu_group_factor(double (&a)[Group<N, T>::K][N],
                 const bool live = !zero && i > k && i < N;
                 if (live) {
 #pragma unroll
-                    for (int j = k + 1; j < N; ++j) a[s][j] = __fma_rn(a[s][k], uk[j], a[s][j]);
+                    for (int j = k + 2; j < N; ++j) a[s][j] = __fma_rn(a[s][k], uk[j], a[s][j]);
                     if (NB > 0) b[s] = __fma_rn(a[s][k], uk[N], b[s]);
                 }
             }

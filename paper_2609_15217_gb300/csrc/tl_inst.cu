@@ -18,9 +18,12 @@ template <int N, int T, int L>
 void reg_one_layout()
 {
     if constexpr (T == 1) {
-        register_variant(N, L, kOpGesv, 1, reinterpret_cast<const void *>(&k_factor_thread<N, L, kGesv, false>));
-        register_variant(N, L, kOpGesvLU, 1, reinterpret_cast<const void *>(&k_factor_thread<N, L, kGesv, true>));
-        register_variant(N, L, kOpGetrf, 1, reinterpret_cast<const void *>(&k_factor_thread<N, L, kGetrf, true>));
+        register_variant(N, L, kOpGesv, 1, reinterpret_cast<const void *>(&k_factor_thread<N, L, kGesv, false>), 0,
+                         reinterpret_cast<const void *>(&k_fixup_thread<N, L, kGesv, false>));
+        register_variant(N, L, kOpGesvLU, 1, reinterpret_cast<const void *>(&k_factor_thread<N, L, kGesv, true>), 0,
+                         reinterpret_cast<const void *>(&k_fixup_thread<N, L, kGesv, true>));
+        register_variant(N, L, kOpGetrf, 1, reinterpret_cast<const void *>(&k_factor_thread<N, L, kGetrf, true>), 0,
+                         reinterpret_cast<const void *>(&k_fixup_thread<N, L, kGetrf, true>));
         register_variant(N, L, kOpGetrs, 1, reinterpret_cast<const void *>(&k_getrs_thread<N, L>));
     } else {
         register_variant(N, L, kOpGesv, T, reinterpret_cast<const void *>(&k_factor_group<N, T, L, kGesv, false>));
@@ -38,7 +41,8 @@ struct Registrar {
         // ragged batches are per-system storage only; registered in slot 0
         if constexpr (TL_INST_T == 1)
             register_variant(TL_INST_N, kPerSystem, kOpRagged, 1,
-                             reinterpret_cast<const void *>(&k_ragged_thread<TL_INST_N>));
+                             reinterpret_cast<const void *>(&k_ragged_thread<TL_INST_N>), 0,
+                             reinterpret_cast<const void *>(&k_ragged_fixup<TL_INST_N>));
         else
             register_variant(TL_INST_N, kPerSystem, kOpRagged, TL_INST_T,
                              reinterpret_cast<const void *>(&k_ragged_group<TL_INST_N, TL_INST_T>));

@@ -51,6 +51,7 @@ struct Variant {
     int lanes;                     // T
     const void *kernel;            // __global__ function, for occupancy queries
     int kind;
+    const void *fixup;             // second pass for flagged systems (or null)
 };
 __host__ __device__ constexpr int variant_id(int lanes, int kind) { return lanes + 100 * kind; }
 
@@ -63,6 +64,7 @@ struct VariantList {
     Variant v[kMaxVariants];
 };
 VariantList &registry(int n, int layout, int op);
-void register_variant(int n, int layout, int op, int lanes, const void *kernel, int kind = 0);
+void register_variant(int n, int layout, int op, int lanes, const void *kernel, int kind = 0,
+                      const void *fixup = nullptr);
 
 }  // namespace tl

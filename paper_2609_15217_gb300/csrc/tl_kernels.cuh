@@ -27,6 +27,11 @@ struct Idx {
     }
 };
 
+// info value the fast one-thread kernels leave for a system that must be
+// redone by the exact general path; the fixup kernel that runs right after
+// them on the same stream replaces it, so callers never see it.
+constexpr int32_t kInfoSlow = -2147483000;
+
 // Streaming loads/stores: every input is read once and every output written
 // once, so keep them out of the way of the L2 lines that are reused.
 __device__ __forceinline__ double ld_stream(const double *p) { return __ldcs(p); }
@@ -37,6 +42,53 @@ __device__ __forceinline__ void st_stream(int32_t *p, int32_t v) { __stcs(p, v);
 // One thread per system.
 // MODE: kGesv (A const, LU_out optional via KEEP), kGetrf (A in place).
 // ---------------------------------------------------------------------------
+// Exact general path for one system (zero, tiny, huge or non-finite pivots
+// or inputs): loads the system again, factors it with lu_thread_factor and
+// stores every output.
+template <int N, int LAYOUT, int MODE, bool KEEP>
+__device__ __forceinline__ void slow_factor_thread(SolveArgs args, int64_t s)
+{
+    using I = Idx<N, LAYOUT>;
+    const double *A = (MODE == kGetrf) ? args.LU : args.A;
+    double a[N][N];
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+#pragma unroll
+        for (int i = 0; i < N; ++i) a[i][j] = A[I::a(s, i, j, args.ld)];
+    double b[1][N];
+    if (MODE == kGesv) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) b[0][i] = args.b[I::v(s, i, args.ld)];
+    }
+    const bool bad = dev::any_nonfinite<N>(a);
+    int piv[N];
+    double rcp[N];
+    bool tiny = false;
+    int info = dev::lu_thread_factor<N, KEEP, (MODE == kGesv) ? 1 : 0>(a, b, piv, rcp, tiny);
+    if (MODE == kGesv) dev::lu_thread_backsolve<N>(a, b[0], rcp, tiny);
+    if (bad) info = -1;
+    if (MODE == kGesv) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) args.x[I::v(s, i, args.ld)] = info != 0 ? dev::nan_value() : b[0][i];
+    }
+    if (KEEP) {
+        // info = -1: nothing is factored; the factors output keeps A.
+        if (!bad) {
+            dev::lu_thread_unnegate_L<N>(a);
+#pragma unroll
+            for (int j = 0; j < N; ++j)
+#pragma unroll
+                for (int i = 0; i < N; ++i) args.LU[I::a(s, i, j, args.ld)] = a[i][j];
+        } else if (MODE == kGesv) {
+            for (int j = 0; j < N; ++j)
+                for (int i = 0; i < N; ++i) args.LU[I::a(s, i, j, args.ld)] = args.A[I::a(s, i, j, args.ld)];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < N; ++k) args.ipiv[I::v(s, k, args.ld)] = bad ? k + 1 : piv[k] + 1;
+    args.info[s] = info;
+}
+
 template <int N, int LAYOUT, int MODE, bool KEEP>
 __global__ void __launch_bounds__(128) k_factor_thread(SolveArgs args)
 {
@@ -55,36 +107,43 @@ __global__ void __launch_bounds__(128) k_factor_thread(SolveArgs args)
 #pragma unroll
         for (int i = 0; i < N; ++i) b[0][i] = ld_stream(args.b + I::v(s, i, args.ld));
     }
+    // Branch-free fast path; a system with a zero, tiny, huge or non-finite
+    // pivot (or input) is redone from its input by the exact general path.
     const bool bad = dev::any_nonfinite<N>(a);
     int piv[N];
     double rcp[N];
-    bool tiny = false;
-    int info = dev::lu_thread_factor<N, KEEP, (MODE == kGesv) ? 1 : 0>(a, b, piv, rcp, tiny);
-    if (MODE == kGesv) dev::lu_thread_backsolve<N>(a, b[0], rcp, tiny);
-    if (bad) info = -1;
-
-    if (MODE == kGesv) {
+    const bool slow = dev::lu_thread_factor_fast<N, KEEP, (MODE == kGesv) ? 1 : 0>(a, b, piv, rcp) || bad;
+    if (!slow) {
+        if (MODE == kGesv) {
+            dev::lu_thread_backsolve_fast<N>(a, b[0], rcp);
 #pragma unroll
-        for (int i = 0; i < N; ++i)
-            st_stream(args.x + I::v(s, i, args.ld), info != 0 ? dev::nan_value() : b[0][i]);
-    }
-    if (KEEP) {
-        // info = -1: nothing is factored; the factors output keeps A.
-        double *LU = args.LU;
-        if (!bad) {
+            for (int i = 0; i < N; ++i) st_stream(args.x + I::v(s, i, args.ld), b[0][i]);
+        }
+        if (KEEP) {
             dev::lu_thread_unnegate_L<N>(a);
 #pragma unroll
             for (int j = 0; j < N; ++j)
 #pragma unroll
-                for (int i = 0; i < N; ++i) st_stream(LU + I::a(s, i, j, args.ld), a[i][j]);
-        } else if (MODE == kGesv) {
-            for (int j = 0; j < N; ++j)
-                for (int i = 0; i < N; ++i) LU[I::a(s, i, j, args.ld)] = args.A[I::a(s, i, j, args.ld)];
+                for (int i = 0; i < N; ++i) st_stream(args.LU + I::a(s, i, j, args.ld), a[i][j]);
         }
-    }
 #pragma unroll
-    for (int k = 0; k < N; ++k) st_stream(args.ipiv + I::v(s, k, args.ld), bad ? k + 1 : piv[k] + 1);
-    st_stream(args.info + s, info);
+        for (int k = 0; k < N; ++k) st_stream(args.ipiv + I::v(s, k, args.ld), piv[k] + 1);
+        st_stream(args.info + s, 0);
+    } else {
+        args.info[s] = kInfoSlow;  // redone by k_fixup_thread
+    }
+}
+
+// Second pass after k_factor_thread: the systems it flagged go through the
+// exact general path.  A separate kernel so that the general path's registers
+// never weigh on the fast kernel.
+template <int N, int LAYOUT, int MODE, bool KEEP>
+__global__ void __launch_bounds__(128) k_fixup_thread(SolveArgs args)
+{
+    const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (s >= args.batch) return;
+    if (args.info[s] != kInfoSlow) return;
+    slow_factor_thread<N, LAYOUT, MODE, KEEP>(args, s);
 }
 
 // One thread per system: solve with given factors, nrhs right-hand sides.
@@ -106,7 +165,7 @@ __global__ void __launch_bounds__(128) k_getrs_thread(SolveArgs args)
     unsigned long long smallest = ~0ULL;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        rcp[i] = __drcp_rn(a[i][i]);
+        rcp[i] = dev::rcp_rn(a[i][i]);
         unsigned long long m = dev::mag_bits(a[i][i]);
         smallest = m < smallest ? m : smallest;
     }
@@ -230,7 +289,7 @@ __global__ void __launch_bounds__(128) k_getrs_group(SolveArgs args)
 #pragma unroll
         for (int j = 0; j < N; ++j) d = dev::sel(j == i, a[sl][j], d);
         const bool ok = active && i < N;
-        rcp[sl] = __drcp_rn(d);
+        rcp[sl] = dev::rcp_rn(d);
         tiny = tiny || (ok && dev::mag_bits(d) < dev::kDblMinBits);
     }
     for (int r = 0; r < args.nrhs; ++r) {
@@ -282,6 +341,36 @@ __global__ void __launch_bounds__(128) k_getrs_group(SolveArgs args)
 // Ragged batches (tl_lupp_solve_batched): persistent grid-stride kernels over
 // the bucket of systems of size N, each system at its own offsets.
 // ---------------------------------------------------------------------------
+// Exact general path of one ragged system (see slow_factor_thread).
+template <int N>
+__device__ __forceinline__ void slow_ragged_thread(RaggedArgs r, int64_t s)
+{
+    const double *A = r.A + r.a_off[s];
+    const double *bv = r.b + r.b_off[s];
+    double a[N][N];
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+#pragma unroll
+        for (int i = 0; i < N; ++i) a[i][j] = A[j * N + i];
+    double b[1][N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) b[0][i] = bv[i];
+    const bool bad = dev::any_nonfinite<N>(a);
+    int piv[N];
+    double rcp[N];
+    bool tiny = false;
+    int info = dev::lu_thread_factor<N, false, 1>(a, b, piv, rcp, tiny);
+    dev::lu_thread_backsolve<N>(a, b[0], rcp, tiny);
+    if (bad) info = -1;
+    double *x = r.x + r.b_off[s];
+    int32_t *ip = r.ipiv + r.piv_off[s];
+#pragma unroll
+    for (int i = 0; i < N; ++i) x[i] = info != 0 ? dev::nan_value() : b[0][i];
+#pragma unroll
+    for (int k = 0; k < N; ++k) ip[k] = bad ? k + 1 : piv[k] + 1;
+    r.info[s] = info;
+}
+
 template <int N>
 __global__ void __launch_bounds__(128) k_ragged_thread(RaggedArgs r)
 {
@@ -303,17 +392,31 @@ __global__ void __launch_bounds__(128) k_ragged_thread(RaggedArgs r)
         const bool bad = dev::any_nonfinite<N>(a);
         int piv[N];
         double rcp[N];
-        bool tiny = false;
-        int info = dev::lu_thread_factor<N, false, 1>(a, b, piv, rcp, tiny);
-        dev::lu_thread_backsolve<N>(a, b[0], rcp, tiny);
-        if (bad) info = -1;
-        double *x = r.x + r.b_off[s];
-        int32_t *ip = r.ipiv + r.piv_off[s];
+        const bool slow = dev::lu_thread_factor_fast<N, false, 1>(a, b, piv, rcp) || bad;
+        if (!slow) {
+            dev::lu_thread_backsolve_fast<N>(a, b[0], rcp);
+            double *x = r.x + r.b_off[s];
+            int32_t *ip = r.ipiv + r.piv_off[s];
 #pragma unroll
-        for (int i = 0; i < N; ++i) st_stream(x + i, info != 0 ? dev::nan_value() : b[0][i]);
+            for (int i = 0; i < N; ++i) st_stream(x + i, b[0][i]);
 #pragma unroll
-        for (int k = 0; k < N; ++k) st_stream(ip + k, bad ? k + 1 : piv[k] + 1);
-        st_stream(r.info + s, info);
+            for (int k = 0; k < N; ++k) st_stream(ip + k, piv[k] + 1);
+            st_stream(r.info + s, 0);
+        } else {
+            r.info[s] = kInfoSlow;  // redone by k_ragged_fixup
+        }
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(128) k_ragged_fixup(RaggedArgs r)
+{
+    const int64_t beg = r.offsets[N];
+    const int64_t count = r.offsets[N + 1] - beg;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < count; q += stride) {
+        const int64_t s = r.bucket[beg + q];
+        if (r.info[s] == kInfoSlow) slow_ragged_thread<N>(r, s);
     }
 }
 

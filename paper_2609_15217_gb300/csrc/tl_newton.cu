@@ -77,6 +77,31 @@ __device__ __forceinline__ void norton_eval(const NortonParams &P, const double 
     J[6][6] = 1.0;
 }
 
+struct NortonState {
+    double sig0[6], deps[6], x[7];
+};
+struct Solve7 {
+    double dx[7];
+    int info;
+};
+
+// Exact general path of one Newton solve (a zero, tiny, huge or non-finite
+// pivot met by the fast path): rebuild F and J at x and solve with the
+// general LUpp.  Out of line so that it does not weigh on the fast path.
+static __device__ __noinline__ Solve7 slow_norton_solve(NortonParams P, NortonState st)
+{
+    double F[7], J[7][7], sig[6], rhs[7];
+    norton_eval(P, st.sig0, st.deps, st.x, F, J, sig);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) rhs[i] = dev::neg(F[i]);
+    int piv[7];
+    Solve7 out;
+    out.info = dev::lupp_solve<7>(J, rhs, piv);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) out.dx[i] = rhs[i];
+    return out;
+}
+
 template <int N>
 __device__ __forceinline__ double norm2(const double (&F)[N])
 {
@@ -124,7 +149,21 @@ __global__ void __launch_bounds__(128) k_newton_norton(NortonParams P, int64_t n
 #pragma unroll
             for (int i = 0; i < 7; ++i) rhs[i] = dev::neg(F[i]);
             int piv[7];
-            const int info = dev::lupp_solve<7>(J, rhs, piv);
+            int info = 0;
+            if (!dev::lupp_solve_fast<7>(J, rhs, piv)) {
+                NortonState ns;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    ns.sig0[i] = sig0[i];
+                    ns.deps[i] = deps[i];
+                }
+#pragma unroll
+                for (int i = 0; i < 7; ++i) ns.x[i] = x[i];
+                const Solve7 o = slow_norton_solve(P, ns);
+                info = o.info;
+#pragma unroll
+                for (int i = 0; i < 7; ++i) rhs[i] = o.dx[i];
+            }
             if (info != 0) {
                 st = TL_NEWTON_SINGULAR;
             } else {
@@ -154,6 +193,45 @@ __global__ void __launch_bounds__(128) k_newton_norton(NortonParams P, int64_t n
 // memory (L1/L2-resident) at every iteration because the factorization
 // overwrites the Jacobian in registers.
 constexpr int kTanhThreadMaxN = 9;
+
+template <int N>
+struct VecN {
+    double v[N];
+};
+template <int N>
+struct SolveN {
+    double dx[N];
+    int info;
+};
+
+// Exact general path of one tanh-law solve (see slow_norton_solve).
+template <int N>
+static __device__ __noinline__ SolveN<N> slow_tanh_solve(const double *__restrict__ in, int64_t npoints, int64_t p,
+                                                         VecN<N> x)
+{
+    double J[N][N], rhs[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const double ti = tanh(x.v[i]);
+        const double ci = in[(N * N + i) * npoints + p];
+        const double bi = in[(N * N + N + i) * npoints + p];
+        double acc = 0.0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const double aij = in[(j * N + i) * npoints + p];
+            acc = fma(aij, x.v[j], acc);
+            J[i][j] = aij;
+        }
+        rhs[i] = dev::neg(fma(ci, ti, acc) - bi);
+        J[i][i] = fma(ci, fma(-ti, ti, 1.0), J[i][i]);
+    }
+    int piv[N];
+    SolveN<N> out;
+    out.info = dev::lupp_solve<N>(J, rhs, piv);
+#pragma unroll
+    for (int i = 0; i < N; ++i) out.dx[i] = rhs[i];
+    return out;
+}
 
 template <int N>
 __global__ void __launch_bounds__(128) k_newton_tanh(int64_t npoints, const double *__restrict__ in,
@@ -201,7 +279,16 @@ __global__ void __launch_bounds__(128) k_newton_tanh(int64_t npoints, const doub
 #pragma unroll
             for (int i = 0; i < N; ++i) rhs[i] = dev::neg(F[i]);
             int piv[N];
-            const int info = dev::lupp_solve<N>(J, rhs, piv);
+            int info = 0;
+            if (!dev::lupp_solve_fast<N>(J, rhs, piv)) {
+                VecN<N> xv;
+#pragma unroll
+                for (int i = 0; i < N; ++i) xv.v[i] = x[i];
+                const SolveN<N> o = slow_tanh_solve<N>(in, npoints, p, xv);
+                info = o.info;
+#pragma unroll
+                for (int i = 0; i < N; ++i) rhs[i] = o.dx[i];
+            }
             if (info != 0) {
                 st = TL_NEWTON_SINGULAR;
             } else {

@@ -134,6 +134,8 @@ tl_status ragged_solve(tl_handle *h, int64_t batch, const int32_t *n, RaggedArgs
         int64_t g = need < resident ? need : resident;
         void *params[] = {&r};
         e = cudaLaunchKernel(v->kernel, dim3(static_cast<unsigned>(g)), dim3(blk), params, 0, stream);
+        if (e == cudaSuccess && v->fixup)
+            e = cudaLaunchKernel(v->fixup, dim3(static_cast<unsigned>(g)), dim3(blk), params, 0, stream);
         if (e != cudaSuccess) return fail_cuda(h, e);
     }
     return TL_OK;

@@ -26,9 +26,20 @@
 
 namespace tl {
 
-// Shared-memory footprint of one system (bytes, 16-byte multiple).
-__host__ __device__ constexpr int smem_sys_doubles(int n) { return n * (n + 1) + 32 + 32; }
-__host__ __device__ constexpr size_t smem_sys_bytes(int n) { return static_cast<size_t>(smem_sys_doubles(n)) * 8; }
+// Shared-memory footprint of one system in doubles: the n x (n+1) block,
+// 32 reciprocals, 32 + 32 ints (row table, pivots).  Padded so that the
+// systems of one half-warp (16 lanes of 8-byte accesses) start T banks apart
+// and their lanes do not collide on the same bank.
+__host__ __device__ constexpr int smem_sys_doubles(int n, int T = 16)
+{
+    const int base = n * (n + 1) + 32 + 32;
+    const int want = (T < 16) ? T : 0;
+    return base + ((want - base % 16) % 16 + 16) % 16;
+}
+__host__ __device__ constexpr size_t smem_sys_bytes(int n, int T = 16)
+{
+    return static_cast<size_t>(smem_sys_doubles(n, T)) * 8;
+}
 
 template <int T>
 __device__ __forceinline__ int group_any_int(int v)
@@ -44,7 +55,7 @@ __global__ void __launch_bounds__(128) k_smem_group(SolveArgs args, int n)
 {
     extern __shared__ double smem[];
     const int SB = blockDim.x / T;                 // systems per block
-    const int per = smem_sys_doubles(n);
+    const int per = smem_sys_doubles(n, T);
     const int RS = n + 1;                          // row stride
     const int64_t s0 = static_cast<int64_t>(blockIdx.x) * SB;
     const double *Ag = (MODE == kGetrf) ? args.LU : args.A;
@@ -133,7 +144,7 @@ __global__ void __launch_bounds__(128) k_smem_group(SolveArgs args, int n)
         const int rk = perm[k];
         // a4: reciprocal and negated multipliers
         const bool small = !zero && dev::mag_bits(cv) < dev::kDblMinBits;
-        const double r = __drcp_rn(cv);
+        const double r = dev::rcp_rn(cv);
         if (t == 0) rcp[k] = r;
         tiny = tiny || small;
         const double nr = dev::neg(r);
@@ -156,21 +167,30 @@ __global__ void __launch_bounds__(128) k_smem_group(SolveArgs args, int n)
             const int w = wcols - k - 1;
             const int total = m * w;
             if (total > 0) {
+                // each lane walks elements e = t, t+T, ... of the flattened
+                // m x w block, four at a time: all loads of a group are issued
+                // before its FMAs (the four elements are distinct, so the
+                // reordering is exact; the compiler cannot prove it alone)
                 int ii = t / w, jj = t % w;
-                int row = (t < total) ? perm[k + 1 + ii] : 0;
-                double l = (t < total) ? M[row * RS + k] : 0.0;
                 const double *urow = M + rk * RS + k + 1;
-                for (int e = t; e < total; e += T) {
-                    double *a = &M[row * RS + k + 1 + jj];
-                    *a = __fma_rn(l, urow[jj], *a);
-                    jj += T;
-                    if (jj >= w) {
-                        do { jj -= w; ++ii; } while (jj >= w);
-                        if (e + T < total) {
-                            row = perm[k + 1 + ii];
-                            l = M[row * RS + k];
-                        }
+                for (int e = t; e < total; e += 4 * T) {
+                    int off[4];
+                    double l[4], u[4], a[4];
+#pragma unroll
+                    for (int q2 = 0; q2 < 4; ++q2) {
+                        const bool ok = e + q2 * T < total;
+                        const int row = ok ? perm[k + 1 + ii] : rk;
+                        off[q2] = ok ? row * RS + k + 1 + jj : -1;
+                        l[q2] = ok ? M[row * RS + k] : 0.0;
+                        u[q2] = ok ? urow[jj] : 0.0;
+                        jj += T;
+                        while (jj >= w) { jj -= w; ++ii; }
                     }
+#pragma unroll
+                    for (int q2 = 0; q2 < 4; ++q2) a[q2] = off[q2] >= 0 ? M[off[q2]] : 0.0;
+#pragma unroll
+                    for (int q2 = 0; q2 < 4; ++q2)
+                        if (off[q2] >= 0) M[off[q2]] = __fma_rn(l[q2], u[q2], a[q2]);
                 }
             }
         }
