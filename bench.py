@@ -86,7 +86,7 @@ FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12
 # DRAM bytes per system measured by ncu for the current kernels
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch / systems);
 # an entry must be removed whenever its kernel changes.
-DRAM_BYTES_PER_SYSTEM = {8: 651, 32: 8843}
+DRAM_BYTES_PER_SYSTEM = {}
 
 
 def load_peaks():
@@ -283,8 +283,10 @@ NORTON_EVAL_FLOPS = 244
 NORTON_LU_FLOPS = flops_per_system(7)
 
 
-def newton_bench(tl, h, steps, warmup, torch, device, I, seed, npoints=NEWTON_POINTS):
-    """Fused Norton Newton over npoints (n = 7): points/s and FP64 fraction."""
+def newton_bench(tl, h, steps, warmup, torch, device, I, seed, npoints=NEWTON_POINTS, cpu_driven_steps=3):
+    """Norton Newton over npoints (n = 7): the fused per-point kernel
+    (Algorithm 2) in points/s with its FP64 fraction, and the batched,
+    CPU-driven loop (Algorithm 1) on the same points beside it."""
     sig0, deps = I.norton_points_torch(npoints, seed, device)
     fields = torch.cat([sig0.t(), deps.t()], dim=0).contiguous()  # (12, npoints)
     del sig0, deps
@@ -295,33 +297,46 @@ def newton_bench(tl, h, steps, warmup, torch, device, I, seed, npoints=NEWTON_PO
     law = tl.make_law(tl.TL_LAW_NORTON, 7, (200000.0, 0.3, 1e-12, 4.0, 1.0))
     stream = torch.cuda.current_stream()
 
-    def run():
-        r = tl.tl_newton_integrate(h, law, npoints, fields, x, sig, it, st, 1e-10, 20, stream.cuda_stream)
-        if r != 0:
-            tl.check("tl_newton_integrate", r, h)
+    def timed(entry, name, k, w):
+        def run():
+            r = entry(h, law, npoints, fields, x, sig, it, st, 1e-10, 20, stream.cuda_stream)
+            if r != 0:
+                tl.check(name, r, h)
+        for _ in range(w):
+            run()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ms = []
+        for _ in range(k):
+            e0.record(stream)
+            run()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
 
-    for _ in range(warmup):
-        run()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    ms = []
-    for _ in range(steps):
-        e0.record(stream)
-        run()
-        e1.record(stream)
-        e1.synchronize()
-        ms.append(e0.elapsed_time(e1))
-    med = statistics.median(ms)
+    med = timed(tl.tl_newton_integrate, "tl_newton_integrate", steps, warmup)
     iters = it.to(torch.int64)
     total_it = int(iters.sum().item())
     flops = total_it * NORTON_LU_FLOPS + (total_it + npoints) * NORTON_EVAL_FLOPS
     status = torch.bincount(st.to(torch.int64), minlength=4).tolist()
-    return {"points": npoints, "ms": med, "points_per_s": npoints / (med / 1e3),
-            "mean_iterations": total_it / npoints, "max_iterations": int(iters.max().item()),
-            "status_counts": status[:4], "fp64_tflops": flops / (med / 1e3) / 1e12,
-            "fp64_frac": flops / (med / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
-            "flops_model": "per solve 300 (LU n=7) + per law evaluation 244"}
+    out = {"points": npoints, "ms": med, "points_per_s": npoints / (med / 1e3),
+           "mean_iterations": total_it / npoints, "max_iterations": int(iters.max().item()),
+           "status_counts": status[:4], "fp64_tflops": flops / (med / 1e3) / 1e12,
+           "fp64_frac": flops / (med / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+           "flops_model": "per solve 300 (LU n=7) + per law evaluation 244"}
+    if cpu_driven_steps > 0:
+        x_f, it_f, st_f = x.clone(), it.clone(), st.clone()
+        med_cd = timed(tl.tl_newton_integrate_cpu_driven, "tl_newton_integrate_cpu_driven", cpu_driven_steps, 1)
+        same = bool(torch.equal(it, it_f) and torch.equal(st, st_f) and
+                    torch.equal(x.view(torch.int64), x_f.view(torch.int64)))
+        out["cpu_driven"] = {"ms": med_cd, "points_per_s": npoints / (med_cd / 1e3),
+                             "fused_speedup": med_cd / med, "iterations": int(iters.max().item()) + 1,
+                             "results_equal_fused": same,
+                             "launches_per_iteration": "assemble + gesv (+ fixup) + update, D2H count"}
+        del x_f, it_f, st_f
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -518,8 +533,10 @@ def main():
                          "per-n batch sizes"}
 
     log("done")
+    # one launch per n and step, plus the fixup launch that follows the
+    # one-thread register kernels (variant 1) on the same stream
+    launches = sum(2 if tl.tl_dispatch_get(h, n, 1)[1] == 1 else 1 for n in n_list) * args.steps
     tl.tl_destroy(h)
-    launches = len(n_list) * args.steps
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

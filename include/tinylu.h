@@ -243,6 +243,26 @@ tl_status tl_newton_integrate(tl_handle *h, const tl_law *law, int64_t npoints,
                               cudaStream_t stream);
 
 /*
+ * tl_newton_integrate_cpu_driven -- the batched, CPU-driven evaluation of
+ * the same Newton problem (Algorithm 1; the comparator of the fused kernel,
+ * Sec. 2.4): each iteration launches one kernel that assembles F and J for
+ * every point still iterating and tests convergence, copies the count of
+ * points still iterating to the host and waits for it, then (if any) calls
+ * tl_gesv_batched on all npoints systems -- points that have stopped carry
+ * an identity system -- and launches the update x += dx.
+ * Arguments, initial guess, stopping test and results are those of
+ * tl_newton_integrate; results equal the fused kernel's.  Norton law only
+ * (TL_LAW_TANH returns TL_ERR_UNSUPPORTED).  Synchronizes `stream` once per
+ * iteration; uses the handle's device workspace (about 520 bytes per point,
+ * grown with cudaMalloc on demand) and a pinned host word owned by the
+ * handle; must not run during stream capture.
+ */
+tl_status tl_newton_integrate_cpu_driven(tl_handle *h, const tl_law *law, int64_t npoints,
+                                         const double *inputs, double *x, double *outputs,
+                                         int32_t *iterations, int32_t *status, double rtol,
+                                         int max_iter, cudaStream_t stream);
+
+/*
  * tl_autotune -- time the candidate kernels (thread-to-system mapping and
  * block size) for every n in [n_min, n_max] and the layout on the current
  * device, and keep the fastest per n in the handle's dispatch table (the

@@ -34,7 +34,7 @@ KERNEL_FAMILIES = (
     + [(n, 16) for n in range(25, 33)]
 )
 
-PLAIN_SOURCES = ["tl_api.cu", "tl_newton.cu", "tl_ragged.cu", "tl_noalloc.cu", "tl_inst_smem.cu", "tl_autotune.cu"]
+PLAIN_SOURCES = ["tl_api.cu", "tl_newton.cu", "tl_newton_cpu_driven.cu", "tl_ragged.cu", "tl_noalloc.cu", "tl_inst_smem.cu", "tl_autotune.cu"]
 
 
 def _nvcc():

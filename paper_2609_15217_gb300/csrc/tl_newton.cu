@@ -15,67 +15,10 @@
 #include "tl_device.cuh"
 #include "tl_handle.h"
 #include "tl_internal.h"
+#include "tl_norton.cuh"
 
 namespace tl {
 namespace {
-
-struct NortonParams {
-    double lambda, mu, Acoef, dt;
-    int m;
-};
-
-// Implicit Norton law at one point (J2 flow, isotropic elasticity, Mandel
-// notation: xx, yy, zz, sqrt2*xy, sqrt2*xz, sqrt2*yz; theta = 1):
-//   sig  = sig0 + lambda tr(de) 1 + 2 mu de,  s = dev sig,
-//   seq  = sqrt(3/2 s:s), n = 3/2 s / seq,
-//   F_el = de - deps + dp n,  F_p = dp - dt A seq^m,
-//   dF_el/dde = I + dp (2 mu / seq)(3/2 K - n n^T),  dF_el/ddp = n,
-//   dF_p/dde  = -dt A m seq^(m-1) 2 mu n^T,          dF_p/ddp = 1.
-__device__ __forceinline__ void norton_eval(const NortonParams &P, const double (&sig0)[6],
-                                            const double (&deps)[6], const double (&x)[7],
-                                            double (&F)[7], double (&J)[7][7], double (&sig)[6])
-{
-    const double tr = x[0] + x[1] + x[2];
-    const double two_mu = 2.0 * P.mu;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) sig[i] = sig0[i] + two_mu * x[i];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) sig[i] += P.lambda * tr;
-    const double p3 = (sig[0] + sig[1] + sig[2]) * (1.0 / 3.0);
-    double s[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) s[i] = (i < 3) ? sig[i] - p3 : sig[i];
-    double ss = 0.0;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) ss = fma(s[i], s[i], ss);
-    const double seq = sqrt(1.5 * ss);
-    const double inv = seq > 0.0 ? 1.0 / seq : 0.0;
-    double n[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) n[i] = 1.5 * s[i] * inv;
-    double pw_m1 = 1.0;
-    for (int i = 0; i < P.m - 1; ++i) pw_m1 *= seq;
-    const double pw_m = pw_m1 * seq;
-    const double dp = x[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) F[i] = fma(dp, n[i], x[i] - deps[i]);
-    F[6] = dp - P.dt * P.Acoef * pw_m;
-
-    const double c = dp * two_mu * inv;
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-            const double kij = (i == j ? 1.0 : 0.0) - ((i < 3 && j < 3) ? 1.0 / 3.0 : 0.0);
-            J[i][j] = (i == j ? 1.0 : 0.0) + c * fma(1.5, kij, -n[i] * n[j]);
-        }
-#pragma unroll
-    for (int i = 0; i < 6; ++i) J[i][6] = n[i];
-    const double g = -P.dt * P.Acoef * P.m * pw_m1 * two_mu;
-#pragma unroll
-    for (int j = 0; j < 6; ++j) J[6][j] = g * n[j];
-    J[6][6] = 1.0;
-}
 
 struct NortonState {
     double sig0[6], deps[6], x[7];
@@ -102,14 +45,6 @@ static __device__ __noinline__ Solve7 slow_norton_solve(NortonParams P, NortonSt
     return out;
 }
 
-template <int N>
-__device__ __forceinline__ double norm2(const double (&F)[N])
-{
-    double s = 0.0;
-#pragma unroll
-    for (int i = 0; i < N; ++i) s = fma(F[i], F[i], s);
-    return sqrt(s);
-}
 
 __global__ void __launch_bounds__(128) k_newton_norton(NortonParams P, int64_t npoints, const double *__restrict__ in,
                                                        double *__restrict__ xout, double *__restrict__ sigout,
@@ -364,24 +299,14 @@ extern "C" tl_status tl_newton_integrate(tl_handle *h, const tl_law *law, int64_
     if (!(rtol >= 0.0)) return fail_arg(h, 9);
     if (max_iter < 0) return fail_arg(h, 10);
     if (law->id == TL_LAW_NORTON) {
-        if (law->n != 7) return fail_arg(h, 2);
-        const double E = law->params[0], nu = law->params[1], Acoef = law->params[2], m = law->params[3],
-                     dt = law->params[4];
-        if (!(E > 0.0) || !(nu > -1.0 && nu < 0.5) || !(m >= 1.0 && m <= 64.0) || m != std::floor(m) ||
-            !std::isfinite(Acoef) || !std::isfinite(dt))
-            return fail_arg(h, 2);
+        NortonParams P;
+        if (!norton_params_from_law(*law, &P)) return fail_arg(h, 2);
         if (npoints == 0) return TL_OK;
         if (!inputs || (reinterpret_cast<uintptr_t>(inputs) & 7)) return fail_arg(h, 4);
         if (!x || (reinterpret_cast<uintptr_t>(x) & 7)) return fail_arg(h, 5);
         if (outputs && (reinterpret_cast<uintptr_t>(outputs) & 7)) return fail_arg(h, 6);
         if (!iterations || (reinterpret_cast<uintptr_t>(iterations) & 3)) return fail_arg(h, 7);
         if (!status || (reinterpret_cast<uintptr_t>(status) & 3)) return fail_arg(h, 8);
-        NortonParams P;
-        P.lambda = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
-        P.mu = E / (2.0 * (1.0 + nu));
-        P.Acoef = Acoef;
-        P.dt = dt;
-        P.m = static_cast<int>(m);
         const void *kern = reinterpret_cast<const void *>(&k_newton_norton);
         const int block = 128;
         int nb = 0;

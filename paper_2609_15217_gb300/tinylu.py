@@ -47,6 +47,8 @@ _SIGS = {
     "tl_lupp_solve_batched": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _int, _vp, _vp], _int),
     "tl_lupp_solve_batched_noalloc": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _int),
     "tl_newton_integrate": ([_vp, C.POINTER(tl_law), _i64, _vp, _vp, _vp, _vp, _vp, C.c_double, _int, _vp], _int),
+    "tl_newton_integrate_cpu_driven": ([_vp, C.POINTER(tl_law), _i64, _vp, _vp, _vp, _vp, _vp, C.c_double, _int,
+                                        _vp], _int),
     "tl_autotune": ([_vp, _int, _int, _int, C.c_char_p], _int),
     "tl_dispatch_set": ([_vp, _int, _int, _int, _int], _int),
     "tl_dispatch_get": ([_vp, _int, _int, C.POINTER(_int), C.POINTER(_int)], _int),
@@ -167,6 +169,12 @@ def make_law(law_id, n, params=()):
 def tl_newton_integrate(h, law, npoints, inputs, x, outputs, iterations, status, rtol, max_iter, stream=None):
     return _lib.tl_newton_integrate(h, C.byref(law), npoints, _p(inputs), _p(x), _p(outputs), _p(iterations),
                                     _p(status), rtol, max_iter, _stream(stream))
+
+
+def tl_newton_integrate_cpu_driven(h, law, npoints, inputs, x, outputs, iterations, status, rtol, max_iter,
+                                   stream=None):
+    return _lib.tl_newton_integrate_cpu_driven(h, C.byref(law), npoints, _p(inputs), _p(x), _p(outputs),
+                                               _p(iterations), _p(status), rtol, max_iter, _stream(stream))
 
 
 def tl_autotune(h, n_min, n_max, layout, table_path=None):
