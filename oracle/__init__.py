@@ -19,6 +19,10 @@ Linear Systems on GPUs: Application to Constitutive Laws"):
   * norton_eval -- the Norton law of Sec. 4.3 (equations not printed in the
     paper; standard implicit J2 + Norton form in Mandel notation).
   * tanh_eval -- synthetic law F(x) = A x + c*tanh(x) - b.
+  * sgetrf / ir_gesv -- binary32 factorization and binary64 iterative
+    refinement (not in the paper: the published scheme of Langou et al.
+    2006, as LAPACK's dsgesv, with every operation's format and order
+    fixed).
 
 Parity pins live in tests/test_oracle_*.py; every function above is pinned
 there by something other than itself (closed forms, exact rational
@@ -55,6 +59,10 @@ def _declare(lib):
     lib.orc_getrf_batch.argtypes = [C.c_int, C.c_int64, _d, _i32, _i32, _d, C.c_int]
     lib.orc_getrs_batch.restype = None
     lib.orc_getrs_batch.argtypes = [C.c_int, C.c_int64, _d, _i32, _d, C.c_int]
+    lib.orc_sgetrf.restype = C.c_int
+    lib.orc_sgetrf.argtypes = [C.c_int, C.POINTER(C.c_float), _i32]
+    lib.orc_ir_gesv_batch.restype = None
+    lib.orc_ir_gesv_batch.argtypes = [C.c_int, C.c_int64, _d, _d, _d, _i32, _i32, _i32, C.c_int]
     lib.orc_norton_eval.restype = None
     lib.orc_norton_eval.argtypes = [_d, _d, _d, _d, _d, _d, _d]
     lib.orc_tanh_eval.restype = None
@@ -138,6 +146,39 @@ def gesv(A, b, want_lu=False, nthreads=0, lib=None):
     if want_lu:
         return x, ipiv, info, gap, _mathidx(lu)
     return x, ipiv, info, gap
+
+
+def sgetrf(A, lib=None):
+    """Binary32 LUpp of each A[s] (float32 input, math-indexed) with the
+    steps of getrf; stops at a pivot outside [FLT_MIN, Inf).  Returns
+    (LU (float32), ipiv, ok) where ok[s] is False for a stopped system."""
+    lib = lib or load()
+    Acm = np.ascontiguousarray(np.asarray(A, np.float32).transpose(0, 2, 1))
+    batch, n = Acm.shape[0], Acm.shape[1]
+    ipiv = np.zeros((batch, n), np.int32)
+    ok = np.zeros(batch, bool)
+    for s in range(batch):
+        ok[s] = lib.orc_sgetrf(n, Acm[s].ctypes.data_as(C.POINTER(C.c_float)),
+                               ipiv[s].ctypes.data_as(_i32)) == 0
+    return np.ascontiguousarray(Acm.transpose(0, 2, 1)), ipiv, ok
+
+
+def ir_gesv(A, b, nthreads=0, lib=None):
+    """Mixed-precision solve of every A[s] x[s] = b[s]: binary32 factor,
+    binary64 iterative refinement (at most 3 corrections), binary64 LUpp
+    fallback.  Returns (x, ipiv, info, steps); steps[s] = -1 marks a system
+    solved by gesv instead."""
+    lib = lib or load()
+    Acm = _colmajor(A)
+    batch, n = Acm.shape[0], Acm.shape[1]
+    b = np.ascontiguousarray(np.asarray(b, np.float64).reshape(batch, n))
+    x = np.empty((batch, n), np.float64)
+    ipiv = np.zeros((batch, n), np.int32)
+    info = np.zeros(batch, np.int32)
+    steps = np.zeros(batch, np.int32)
+    lib.orc_ir_gesv_batch(n, batch, _ptr(Acm), _ptr(b), _ptr(x), _ptr(ipiv, _i32), _ptr(info, _i32),
+                          _ptr(steps, _i32), nthreads)
+    return x, ipiv, info, steps
 
 
 def norton_params(E=200000.0, nu=0.3, A=1e-12, m=4, dt=1.0):

@@ -29,6 +29,9 @@
  *                  Norton form is used, see the module docstring of the
  *                  Python wrapper for the reading).
  *   orc_tanh_eval -- synthetic law F(x) = A x + c .* tanh(x) - b.
+ *   orc_sgetrf / orc_sgetrs / orc_ir_solve -- binary32 factorization with
+ *                  binary64 iterative refinement (not in the paper; the
+ *                  published scheme of Langou et al. 2006, see below).
  *
  * Readings where the paper is silent (pivot tie-break, multiplier arithmetic,
  * zero and non-finite pivots, pivot base) are listed beside each function.
@@ -247,6 +250,193 @@ void orc_getrs_batch(int n, int64_t batch, const double *LU, const int32_t *ipiv
 #endif
     for (int64_t s = 0; s < batch; ++s)
         orc_getrs(n, LU + (size_t)s * nn, ipiv + (size_t)s * n, B + (size_t)s * n);
+    (void)nthreads;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Mixed precision: binary32 factorization, binary64 refinement            */
+/* ---------------------------------------------------------------------- */
+/*
+ * The paper factors in binary64 only.  The mixed-precision variant follows
+ * the published iterative-refinement scheme of Langou et al. (2006), the
+ * one of LAPACK's dsgesv: factor a binary32 copy of A, solve in binary32,
+ * then correct the binary64 solution with binary64 residuals and binary32
+ * correction solves, falling back to the binary64 LUpp when refinement does
+ * not converge.  Every operation below is a single IEEE round-to-nearest
+ * operation in the stated format, in the stated order, so that a GPU
+ * implementation can reproduce each result bit for bit.
+ */
+
+/* |a| > |b| for binary32 with NaN ranked above every number (as mag_greater). */
+static int mag_greater_f(float a, float b)
+{
+    if (isnan(a)) return !isnan(b);
+    if (isnan(b)) return 0;
+    return fabsf(a) > fabsf(b);
+}
+
+/* FLT_MIN <= |v| < Inf (a usable binary32 pivot). */
+static int usable_f(float v) { return fabsf(v) >= FLT_MIN && fabsf(v) < INFINITY; }
+
+/*
+ * orc_sgetrf: binary32 PA = LU with the steps of orc_getrf (first maximum,
+ * full row swaps, l_ik = a_ik * RN32(1/a_kk), a_ij = fmaf(-l_ik, a_kj, a_ij)).
+ * No sfmin branch and no zero-pivot continuation: a pivot that is not in
+ * [FLT_MIN, Inf) (zero, subnormal, Inf or NaN) stops the factorization and
+ * returns 1 -- the caller then solves in binary64.  Returns 0 otherwise.
+ */
+int orc_sgetrf(int n, float *a, int32_t *ipiv)
+{
+    for (int k = 0; k < n; ++k) {
+        int p = k;
+        for (int i = k + 1; i < n; ++i)
+            if (mag_greater_f(AT(a, n, i, k), AT(a, n, p, k))) p = i;
+        ipiv[k] = p + 1;
+        if (!usable_f(AT(a, n, p, k))) return 1;
+        if (p != k)
+            for (int j = 0; j < n; ++j) {
+                float t = AT(a, n, k, j);
+                AT(a, n, k, j) = AT(a, n, p, j);
+                AT(a, n, p, j) = t;
+            }
+        float r = 1.0f / AT(a, n, k, k);
+        for (int i = k + 1; i < n; ++i) AT(a, n, i, k) = AT(a, n, i, k) * r;
+        for (int j = k + 1; j < n; ++j)
+            for (int i = k + 1; i < n; ++i)
+                AT(a, n, i, j) = fmaf(-AT(a, n, i, k), AT(a, n, k, j), AT(a, n, i, j));
+    }
+    return 0;
+}
+
+/*
+ * orc_sgetrs: binary32 solve with the factors of orc_sgetrf: interchanges in
+ * order k = 0..n-1, forward y_i = fmaf(-l_ij, y_j, y_i) in increasing j, back
+ * s = fmaf(-u_ij, y_j, s) in decreasing j, then y_i = s * RN32(1/u_ii) (a
+ * multiplication by the rounded reciprocal, not a division).  Returns 1 if a
+ * result is NaN or +-Inf, else 0.
+ */
+int orc_sgetrs(int n, const float *lu, const int32_t *ipiv, float *y)
+{
+    for (int k = 0; k < n; ++k) {
+        int p = ipiv[k] - 1;
+        if (p != k) {
+            float t = y[k];
+            y[k] = y[p];
+            y[p] = t;
+        }
+    }
+    for (int i = 1; i < n; ++i) {
+        float s = y[i];
+        for (int j = 0; j < i; ++j) s = fmaf(-AT(lu, n, i, j), y[j], s);
+        y[i] = s;
+    }
+    int bad = 0;
+    for (int i = n - 1; i >= 0; --i) {
+        float s = y[i];
+        for (int j = n - 1; j > i; --j) s = fmaf(-AT(lu, n, i, j), y[j], s);
+        y[i] = s * (1.0f / AT(lu, n, i, i));
+        if (!isfinite(y[i])) bad = 1;
+    }
+    return bad;
+}
+
+/*
+ * orc_ir_solve: the mixed-precision solve of one system.
+ *   1. A must be finite, and every nonzero a_ij must round to a binary32
+ *      value in [FLT_MIN, FLT_MAX]: a32_ij = RN32(a_ij).
+ *   2. anrm = max_i of the binary32 sum, in increasing j, of |a32_ij|; it
+ *      must be finite.  cte = RN64(anrm * RN64(sqrt(n) * 2^-53)).
+ *   3. orc_sgetrf(a32) must succeed.
+ *   4. x = widen(orc_sgetrs(RN32(b))), which must be finite.
+ *   5. for it = 0, 1, ...:
+ *        r_i = b_i, then r_i = fma(-a_ij, x_j, r_i) for j = 0..n-1 (binary64);
+ *        converged when max_i |r_i| <= RN64(max_i |x_i| * cte): steps = it;
+ *        at it = 3 without convergence, stop (binary64 fallback);
+ *        d = orc_sgetrs(RN32(r)), which must be finite;
+ *        x_i = RN64(x_i + widen(d_i)).
+ * Returns 0 with x, ipiv (the binary32 pivots, 1-based) and *steps set, or
+ * 1 when any condition fails: the caller then solves with orc_gesv.
+ * wf holds n*n + n floats.
+ */
+int orc_ir_solve(int n, const double *a, const double *b, double *x, int32_t *ipiv, int *steps,
+                 float *wf)
+{
+    float *a32 = wf;
+    float *y = wf + (size_t)n * (size_t)n;
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            const double v = AT(a, n, i, j);
+            if (!isfinite(v)) return 1;
+            const float f = (float)v;
+            if (v != 0.0 && !(fabsf(f) >= FLT_MIN && fabsf(f) <= FLT_MAX)) return 1;
+            AT(a32, n, i, j) = f;
+        }
+    float anrm = 0.0f;
+    for (int i = 0; i < n; ++i) {
+        float rs = 0.0f;
+        for (int j = 0; j < n; ++j) rs = rs + fabsf(AT(a32, n, i, j));
+        if (rs > anrm) anrm = rs;
+    }
+    if (!isfinite(anrm)) return 1;
+    const double cte = (double)anrm * (sqrt((double)n) * 0x1p-53);
+    if (orc_sgetrf(n, a32, ipiv)) return 1;
+    for (int i = 0; i < n; ++i) y[i] = (float)b[i];
+    if (orc_sgetrs(n, a32, ipiv, y)) return 1;
+    for (int i = 0; i < n; ++i) x[i] = (double)y[i];
+    for (int it = 0;; ++it) {
+        double rnrm = 0.0, xnrm = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double r = b[i];
+            for (int j = 0; j < n; ++j) r = fma(-AT(a, n, i, j), x[j], r);
+            y[i] = (float)r;
+            if (isnan(r) || isnan(rnrm)) rnrm = NAN;
+            else if (fabs(r) > rnrm) rnrm = fabs(r);
+            if (fabs(x[i]) > xnrm) xnrm = fabs(x[i]);
+        }
+        if (rnrm <= xnrm * cte) {
+            *steps = it;
+            return 0;
+        }
+        if (it == 3) return 1;
+        if (orc_sgetrs(n, a32, ipiv, y)) return 1;
+        for (int i = 0; i < n; ++i) x[i] = x[i] + (double)y[i];
+    }
+}
+
+/*
+ * Batched mixed-precision solve: steps[s] in 0..3 for a refined system
+ * (info 0, ipiv from the binary32 factor), -1 for a system solved by
+ * orc_gesv instead (ipiv, info and x as orc_gesv gives them).
+ */
+void orc_ir_gesv_batch(int n, int64_t batch, const double *A, const double *b, double *x,
+                       int32_t *ipiv, int32_t *info, int32_t *steps, int nthreads)
+{
+    const size_t nn = (size_t)n * (size_t)n;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel num_threads(nthreads)
+#endif
+    {
+        float *wf = (float *)malloc(sizeof(float) * (nn + (size_t)n + 1));
+        double *work = (double *)malloc(sizeof(double) * (nn ? nn : 1));
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+        for (int64_t s = 0; s < batch; ++s) {
+            const double *as = A + (size_t)s * nn;
+            const double *bs = b + (size_t)s * n;
+            int st = 0;
+            if (orc_ir_solve(n, as, bs, x + (size_t)s * n, ipiv + (size_t)s * n, &st, wf) == 0) {
+                steps[s] = st;
+                info[s] = 0;
+            } else {
+                steps[s] = -1;
+                info[s] = orc_gesv(n, as, bs, x + (size_t)s * n, ipiv + (size_t)s * n, NULL, work, NULL);
+            }
+        }
+        free(wf);
+        free(work);
+    }
     (void)nthreads;
 }
 
