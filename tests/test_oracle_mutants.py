@@ -20,6 +20,7 @@ import oracle
 from oracle import build as obuild
 from paper_2609_15217_gb300 import inputs
 
+from test_oracle_ir import IR_PINS
 from test_oracle_newton import radial_return
 
 EPS = np.finfo(np.float64).eps
@@ -33,15 +34,17 @@ MUTATIONS = {
                     "fma(AT(a, n, i, k), AT(a, n, k, j), AT(a, n, i, j))"),
     "update_transposed": ("fma(-AT(a, n, i, k), AT(a, n, k, j), AT(a, n, i, j))",
                           "fma(-AT(a, n, i, k), AT(a, n, j, k), AT(a, n, i, j))"),
-    "multiplier_perturbed": ("AT(a, n, i, k) = AT(a, n, i, k) * r;",
-                             "AT(a, n, i, k) = AT(a, n, i, k) * r * 1.0000000001;"),
+    "multiplier_perturbed": ("double r = 1.0 / akk;\n            for (int i = k + 1; i < n; ++i) AT(a, n, i, k) = AT(a, n, i, k) * r;",
+                             "double r = 1.0 / akk;\n            for (int i = k + 1; i < n; ++i) AT(a, n, i, k) = AT(a, n, i, k) * r * 1.0000000001;"),
     "no_sfmin_guard": ("if (fabs(akk) >= DBL_MIN) {", "if (1) {"),
     "info_last_zero_pivot": ("if (info == 0) info = k + 1;", "info = k + 1;"),
     "forward_drops_term": ("for (int j = 0; j < i; ++j) s = fma(-AT(lu, n, i, j), b[j], s);",
                            "for (int j = 1; j < i; ++j) s = fma(-AT(lu, n, i, j), b[j], s);"),
     "backsolve_multiplies": ("b[i] = s / AT(lu, n, i, i);", "b[i] = s * AT(lu, n, i, i);"),
-    "rhs_swaps_reversed": ("for (int k = 0; k < n; ++k) {\n        int p = ipiv[k] - 1;",
-                           "for (int k = n - 1; k >= 0; --k) {\n        int p = ipiv[k] - 1;"),
+    "rhs_swaps_reversed": ("for (int k = 0; k < n; ++k) {\n        int p = ipiv[k] - 1;\n        if (p != k) {\n            double t",
+                           "for (int k = n - 1; k >= 0; --k) {\n        int p = ipiv[k] - 1;\n        if (p != k) {\n            double t"),
+    "ir_rhs_swaps_reversed": ("for (int k = 0; k < n; ++k) {\n        int p = ipiv[k] - 1;\n        if (p != k) {\n            float t",
+                              "for (int k = n - 1; k >= 0; --k) {\n        int p = ipiv[k] - 1;\n        if (p != k) {\n            float t"),
     "norton_drops_flow": ("F[i] = de[i] - deps[i] + dp * nrm[i];", "F[i] = de[i] - deps[i];"),
     "norton_jacobian_sign": ("J[i + 7 * j] = (i == j ? 1.0 : 0.0) + c * v;",
                              "J[i + 7 * j] = (i == j ? 1.0 : 0.0) - c * v;"),
@@ -51,6 +54,16 @@ MUTATIONS = {
     "newton_absolute_test": ("if (r <= rtol * r0 || r0 == 0.0)", "if (r <= rtol || r0 == 0.0)"),
     "newton_counts_evals": ("        ++k;\n        eval(ctx, x, F, J);", "        k += 2;\n        eval(ctx, x, F, J);"),
     "tanh_jacobian_sign": ("c[i] * (1.0 - t * t)", "c[i] * (1.0 + t * t)"),
+    "ir_tie_break_last": ("return fabsf(a) > fabsf(b);", "return fabsf(a) >= fabsf(b);"),
+    "ir_l_part_not_swapped": ("for (int j = 0; j < n; ++j) {\n                float t = AT(a, n, k, j);",
+                              "for (int j = k; j < n; ++j) {\n                float t = AT(a, n, k, j);"),
+    "ir_update_sign": ("fmaf(-AT(a, n, i, k), AT(a, n, k, j), AT(a, n, i, j))",
+                       "fmaf(AT(a, n, i, k), AT(a, n, k, j), AT(a, n, i, j))"),
+    "ir_residual_sign": ("for (int j = 0; j < n; ++j) r = fma(-AT(a, n, i, j), x[j], r);",
+                         "for (int j = 0; j < n; ++j) r = fma(AT(a, n, i, j), x[j], r);"),
+    "ir_correction_replaces": ("x[i] = x[i] + (double)y[i];", "x[i] = (double)y[i];"),
+    "ir_one_correction_only": ("if (it == 3) return 1;", "if (it == 1) return 1;"),
+    "ir_absolute_stop": ("if (rnrm <= xnrm * cte) {", "if (rnrm <= cte) {"),
 }
 
 
@@ -153,7 +166,7 @@ def pin_tanh(lib):
         assert np.array_equal(r1["x"], r2["x"])
 
 
-PINS = [pin_golden, pin_reconstruction_and_errors, pin_singular, pin_norton, pin_tanh]
+PINS = [pin_golden, pin_reconstruction_and_errors, pin_singular, pin_norton, pin_tanh, *IR_PINS]
 
 
 def failing_pins(lib):
