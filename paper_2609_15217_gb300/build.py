@@ -34,6 +34,20 @@ KERNEL_FAMILIES = (
     + [(n, 16) for n in range(25, 33)]
 )
 
+# (n, lanes per system) families of the mixed-precision (binary32 factor,
+# binary64 refinement) ragged kernel; binary32 rows take half the registers,
+# so one thread per system reaches further.
+IR_FAMILIES = (
+    [(n, 1) for n in range(1, 11)]
+    + [(n, 4) for n in range(11, 17)]
+    + [(n, 8) for n in range(17, 25)]
+    + [(n, 16) for n in range(25, 33)]
+)
+
+# (n, lanes per point) of the sub-warp tanh-law Newton kernel (n >= 10;
+# smaller n run one thread per point).
+NEWTON_GROUP_FAMILIES = [(n, t) for n, t in KERNEL_FAMILIES if n >= 10]
+
 PLAIN_SOURCES = ["tl_api.cu", "tl_newton.cu", "tl_newton_cpu_driven.cu", "tl_ragged.cu", "tl_noalloc.cu", "tl_inst_smem.cu", "tl_autotune.cu"]
 
 
@@ -61,6 +75,10 @@ def _jobs():
         jobs.append((src, []))
     for n, t in KERNEL_FAMILIES:
         jobs.append(("tl_inst.cu", [f"-DTL_INST_N={n}", f"-DTL_INST_T={t}"]))
+    for n, t in IR_FAMILIES:
+        jobs.append(("tl_inst_ir.cu", [f"-DTL_INST_N={n}", f"-DTL_INST_T={t}"]))
+    for n, t in NEWTON_GROUP_FAMILIES:
+        jobs.append(("tl_inst_newton.cu", [f"-DTL_INST_N={n}", f"-DTL_INST_T={t}"]))
     out = []
     for src, defs in jobs:
         path = os.path.join(CSRC, src)

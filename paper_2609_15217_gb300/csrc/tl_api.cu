@@ -45,6 +45,15 @@ int default_register_lanes(int n)
     return 16;
 }
 
+// Lanes per system of the mixed-precision ragged kernel before any tuning.
+int default_ir_lanes(int n)
+{
+    if (n <= 10) return 1;
+    if (n <= 16) return 4;
+    if (n <= 24) return 8;
+    return 16;
+}
+
 // Default variant id per n before any autotuning.
 int default_lanes(int n) { return variant_id(default_register_lanes(n), 0); }
 

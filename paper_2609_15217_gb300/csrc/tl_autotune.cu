@@ -55,10 +55,11 @@ extern "C" tl_status tl_dispatch_set(tl_handle *h, int n, tl_layout layout, int 
     if (!found) return fail_arg(h, 4);
     for (int op = 0; op < kOps; ++op)
         if (op_takes_variant(op)) h->choice[n][layout][op] = Choice{variant, block};
-    // getrs and the ragged kernels only exist as register kernels: take the
-    // register variant with the same lane count when there is one
+    // getrs and the ragged kernels (binary64 and mixed precision) only exist
+    // as register kernels: take the one with the same lane count when there
+    // is one
     const int lanes = variant % 100;
-    for (int op : {static_cast<int>(kOpGetrs), static_cast<int>(kOpRagged)}) {
+    for (int op : {static_cast<int>(kOpGetrs), static_cast<int>(kOpRagged), static_cast<int>(kOpRaggedIr)}) {
         const VariantList &lo = registry(n, layout, op);
         for (int i = 0; i < lo.count; ++i)
             if (lo.v[i].kind == 0 && lo.v[i].lanes == lanes) h->choice[n][layout][op] = Choice{lanes, 0};

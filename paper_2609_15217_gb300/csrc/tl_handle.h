@@ -28,6 +28,7 @@ struct PairHash {
 
 int default_lanes(int n);
 int default_register_lanes(int n);
+int default_ir_lanes(int n);
 const Variant *find_variant(int n, int layout, int op, int id);
 tl_status fail_arg(tl_handle *h, int pos);
 tl_status fail_cuda(tl_handle *h, cudaError_t e);
@@ -38,8 +39,11 @@ tl_status launch_op(tl_handle *h, int n, int layout, int op, SolveArgs &args, cu
 tl_status ensure_workspace(tl_handle *h, size_t bytes, cudaStream_t stream);
 // Buckets `batch` systems by n[s] using the int32 scratch `ws` (3*64 bin
 // counters followed by `batch` indices) and launches the per-n kernels.
+// With mixed precision the scratch also holds 64 fallback counters and
+// `batch` fallback indices (ragged_ws_ints).
 tl_status ragged_solve(tl_handle *h, int64_t batch, const int32_t *n, RaggedArgs r, int32_t *ws,
-                       cudaStream_t stream);
+                       cudaStream_t stream, bool mixed = false);
+size_t ragged_ws_ints(int64_t batch, bool mixed);
 
 }  // namespace tl
 

@@ -26,8 +26,12 @@ struct SolveArgs {
 };
 
 // Arguments of the ragged-batch kernels (tl_lupp_solve_batched): the
-// systems of size N are listed in bucket[offsets[N] .. offsets[N+1]); each
-// one lives at its own element offsets in per-system column-major storage.
+// systems of size N are listed in bucket[offsets[N] .. offsets[N+1]) -- or
+// bucket[offsets[N] .. offsets[N] + counts[N]) when counts is set; each one
+// lives at its own element offsets in per-system column-major storage.
+// The mixed-precision kernels also write refine (nullable) and append the
+// systems they hand to the binary64 kernels to fb_list[offsets[N] + ...],
+// counting them in fb_count[N].
 struct RaggedArgs {
     const int32_t *bucket;
     const int32_t *offsets;  // [TL_MAX_N + 2]
@@ -39,6 +43,10 @@ struct RaggedArgs {
     const int64_t *piv_off;
     int32_t *ipiv;
     int32_t *info;
+    const int32_t *counts;
+    int32_t *refine;
+    int32_t *fb_count;
+    int32_t *fb_list;
 };
 
 // Kernel variant for one (n, layout, operation): how many lanes share a
@@ -56,8 +64,16 @@ struct Variant {
 __host__ __device__ constexpr int variant_id(int lanes, int kind) { return lanes + 100 * kind; }
 
 // Registry filled by the instantiation units (tl_inst.cu, one per (N, T)).
-enum : int { kOpGesv = 0, kOpGesvLU = 1, kOpGetrf = 2, kOpGetrs = 3, kOpRagged = 4 };
-constexpr int kOps = 5;
+enum : int {
+    kOpGesv = 0,
+    kOpGesvLU = 1,
+    kOpGetrf = 2,
+    kOpGetrs = 3,
+    kOpRagged = 4,
+    kOpRaggedIr = 5,
+    kOpNewtonTanh = 6
+};
+constexpr int kOps = 7;
 constexpr int kMaxVariants = 8;
 struct VariantList {
     int count;

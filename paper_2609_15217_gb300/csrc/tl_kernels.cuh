@@ -341,6 +341,18 @@ __global__ void __launch_bounds__(128) k_getrs_group(SolveArgs args)
 // Ragged batches (tl_lupp_solve_batched): persistent grid-stride kernels over
 // the bucket of systems of size N, each system at its own offsets.
 // ---------------------------------------------------------------------------
+// Number of systems of size N to process: the whole bucket, or the first
+// counts[N] entries of the list when counts is set (never more than the
+// bucket holds).
+template <int N>
+__device__ __forceinline__ int64_t ragged_count(const RaggedArgs &r, int64_t beg)
+{
+    const int64_t full = r.offsets[N + 1] - beg;
+    if (!r.counts) return full;
+    const int64_t c = r.counts[N];
+    return c < 0 ? 0 : (c < full ? c : full);
+}
+
 // Exact general path of one ragged system (see slow_factor_thread).
 template <int N>
 __device__ __forceinline__ void slow_ragged_thread(RaggedArgs r, int64_t s)
@@ -375,7 +387,7 @@ template <int N>
 __global__ void __launch_bounds__(128) k_ragged_thread(RaggedArgs r)
 {
     const int64_t beg = r.offsets[N];
-    const int64_t count = r.offsets[N + 1] - beg;
+    const int64_t count = ragged_count<N>(r, beg);
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < count; q += stride) {
         const int64_t s = r.bucket[beg + q];
@@ -412,7 +424,7 @@ template <int N>
 __global__ void __launch_bounds__(128) k_ragged_fixup(RaggedArgs r)
 {
     const int64_t beg = r.offsets[N];
-    const int64_t count = r.offsets[N + 1] - beg;
+    const int64_t count = ragged_count<N>(r, beg);
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < count; q += stride) {
         const int64_t s = r.bucket[beg + q];
@@ -429,7 +441,7 @@ __global__ void __launch_bounds__(128) k_ragged_group(RaggedArgs r)
     const int t = lane % T;
     const int lane0 = lane - t;
     const int64_t beg = r.offsets[N];
-    const int64_t count = r.offsets[N + 1] - beg;
+    const int64_t count = ragged_count<N>(r, beg);
     const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
     for (int64_t q0 = warp * G; q0 < count; q0 += nwarps * G) {  // warp-uniform loop

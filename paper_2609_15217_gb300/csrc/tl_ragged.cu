@@ -18,7 +18,7 @@ namespace {
 constexpr int kSlots = 64;  // per-bin arrays, indices 0..TL_MAX_N+1 used
 
 __global__ void k_bucket_hist(int64_t batch, const int32_t *__restrict__ n, int32_t *__restrict__ counts,
-                              int32_t *__restrict__ info)
+                              int32_t *__restrict__ info, int32_t *__restrict__ refine)
 {
     __shared__ int32_t sh[kSlots];
     if (threadIdx.x < kSlots) sh[threadIdx.x] = 0;
@@ -26,8 +26,12 @@ __global__ void k_bucket_hist(int64_t batch, const int32_t *__restrict__ n, int3
     const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (s < batch) {
         const int v = n[s];
-        if (v >= 1 && v <= TL_MAX_N) atomicAdd(&sh[v], 1);
-        else info[s] = -2;
+        if (v >= 1 && v <= TL_MAX_N) {
+            atomicAdd(&sh[v], 1);
+        } else {
+            info[s] = -2;
+            if (refine) refine[s] = -1;
+        }
     }
     __syncthreads();
     if (threadIdx.x >= 1 && threadIdx.x <= TL_MAX_N && sh[threadIdx.x] > 0)
@@ -99,46 +103,90 @@ tl_status ensure_workspace(tl_handle *h, size_t bytes, cudaStream_t stream)
     return TL_OK;
 }
 
-// Bucket the batch by size and launch every per-n ragged kernel.  `ws` holds
-// 3 * kSlots int32 bin arrays followed by `batch` int32 indices.
-tl_status ragged_solve(tl_handle *h, int64_t batch, const int32_t *n, RaggedArgs r, int32_t *ws,
-                       cudaStream_t stream)
+size_t ragged_ws_ints(int64_t batch, bool mixed)
 {
-    int32_t *counts = ws;
-    int32_t *offsets = ws + kSlots;
-    int32_t *cursor = ws + 2 * kSlots;
-    int32_t *bucket = ws + 3 * kSlots;
-    cudaError_t e = cudaMemsetAsync(counts, 0, kSlots * sizeof(int32_t), stream);
-    if (e != cudaSuccess) return fail_cuda(h, e);
-    const int block = 256;
-    const unsigned grid = static_cast<unsigned>((batch + block - 1) / block);
-    k_bucket_hist<<<grid, block, 0, stream>>>(batch, n, counts, r.info);
-    k_bucket_scan<<<1, 32, 0, stream>>>(counts, offsets, cursor);
-    k_bucket_scatter<<<grid, block, 0, stream>>>(batch, n, cursor, bucket);
-    if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(h, e);
-    r.bucket = bucket;
-    r.offsets = offsets;
+    return 3 * kSlots + static_cast<size_t>(batch) + (mixed ? kSlots + static_cast<size_t>(batch) : 0);
+}
+
+namespace {
+
+// Persistent grid for one per-n ragged kernel: enough warps for the whole
+// batch (an upper bound on the bucket) but no more than stay resident.
+unsigned ragged_grid(tl_handle *h, const Variant *v, int64_t batch, int blk)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, v->kernel, blk, 0) != cudaSuccess || nb < 1) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    const int64_t need = (batch * v->lanes + blk - 1) / blk;
+    const int64_t resident = static_cast<int64_t>(nb) * h->sm_count;
+    return static_cast<unsigned>(need < resident ? need : resident);
+}
+
+// Binary64 ragged kernels for every n over the lists in r.
+tl_status launch_binary64(tl_handle *h, int64_t batch, RaggedArgs &r, cudaStream_t stream)
+{
     for (int nn = 1; nn <= TL_MAX_N; ++nn) {
         const Choice &c = h->choice[nn][kPerSystem][kOpRagged];
         const Variant *v = find_variant(nn, kPerSystem, kOpRagged, c.lanes ? c.lanes : default_lanes(nn));
         // (ragged launches use the register kernels only)
         if (!v) return TL_ERR_UNSUPPORTED;
         const int blk = 128;
-        int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, v->kernel, blk, 0) != cudaSuccess || nb < 1) {
-            cudaGetLastError();
-            nb = 1;
-        }
-        int64_t need = (batch * v->lanes + blk - 1) / blk;
-        int64_t resident = static_cast<int64_t>(nb) * h->sm_count;
-        int64_t g = need < resident ? need : resident;
+        const unsigned g = ragged_grid(h, v, batch, blk);
         void *params[] = {&r};
-        e = cudaLaunchKernel(v->kernel, dim3(static_cast<unsigned>(g)), dim3(blk), params, 0, stream);
-        if (e == cudaSuccess && v->fixup)
-            e = cudaLaunchKernel(v->fixup, dim3(static_cast<unsigned>(g)), dim3(blk), params, 0, stream);
+        cudaError_t e = cudaLaunchKernel(v->kernel, dim3(g), dim3(blk), params, 0, stream);
+        if (e == cudaSuccess && v->fixup) e = cudaLaunchKernel(v->fixup, dim3(g), dim3(blk), params, 0, stream);
         if (e != cudaSuccess) return fail_cuda(h, e);
     }
     return TL_OK;
+}
+
+}  // namespace
+
+// Bucket the batch by size and launch every per-n ragged kernel.  `ws` holds
+// 3 * kSlots int32 bin arrays followed by `batch` int32 indices, and with
+// mixed precision kSlots fallback counters and `batch` fallback indices.
+tl_status ragged_solve(tl_handle *h, int64_t batch, const int32_t *n, RaggedArgs r, int32_t *ws,
+                       cudaStream_t stream, bool mixed)
+{
+    int32_t *counts = ws;
+    int32_t *offsets = ws + kSlots;
+    int32_t *cursor = ws + 2 * kSlots;
+    int32_t *bucket = ws + 3 * kSlots;
+    cudaError_t e = cudaMemsetAsync(counts, 0, kSlots * sizeof(int32_t), stream);
+    if (e == cudaSuccess && mixed) e = cudaMemsetAsync(bucket + batch, 0, kSlots * sizeof(int32_t), stream);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    const int block = 256;
+    const unsigned grid = static_cast<unsigned>((batch + block - 1) / block);
+    k_bucket_hist<<<grid, block, 0, stream>>>(batch, n, counts, r.info, mixed ? r.refine : nullptr);
+    k_bucket_scan<<<1, 32, 0, stream>>>(counts, offsets, cursor);
+    k_bucket_scatter<<<grid, block, 0, stream>>>(batch, n, cursor, bucket);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(h, e);
+    r.bucket = bucket;
+    r.offsets = offsets;
+    r.counts = nullptr;
+    if (!mixed) return launch_binary64(h, batch, r, stream);
+
+    // mixed precision: binary32 factor + binary64 refinement for every n,
+    // then the binary64 kernels over the systems each size handed back
+    r.fb_count = bucket + batch;
+    r.fb_list = bucket + batch + kSlots;
+    for (int nn = 1; nn <= TL_MAX_N; ++nn) {
+        const Choice &c = h->choice[nn][kPerSystem][kOpRaggedIr];
+        const Variant *v =
+            find_variant(nn, kPerSystem, kOpRaggedIr, c.lanes ? c.lanes : variant_id(default_ir_lanes(nn), 0));
+        if (!v) return TL_ERR_UNSUPPORTED;
+        const int blk = 128;
+        const unsigned g = ragged_grid(h, v, batch, blk);
+        void *params[] = {&r};
+        e = cudaLaunchKernel(v->kernel, dim3(g), dim3(blk), params, 0, stream);
+        if (e != cudaSuccess) return fail_cuda(h, e);
+    }
+    RaggedArgs fb = r;
+    fb.bucket = r.fb_list;
+    fb.counts = r.fb_count;
+    return launch_binary64(h, batch, fb, stream);
 }
 
 }  // namespace tl
@@ -166,11 +214,12 @@ extern "C" tl_status tl_lupp_solve_batched(tl_handle *h, int64_t batch, const in
     if (mis(ipiv, 4)) return fail_arg(h, 10);
     if (mis(info, 4)) return fail_arg(h, 11);
     if (refine_steps && (reinterpret_cast<uintptr_t>(refine_steps) & 3)) return fail_arg(h, 13);
-    if (prec == TL_PREC_FP32_IR) return TL_ERR_UNSUPPORTED;
     if (batch > INT32_MAX) return TL_ERR_UNSUPPORTED;
-    const size_t bytes = (3 * kSlots + static_cast<size_t>(batch)) * sizeof(int32_t);
+    const bool mixed = prec == TL_PREC_FP32_IR;
+    const size_t bytes = ragged_ws_ints(batch, mixed) * sizeof(int32_t);
     tl_status st = ensure_workspace(h, bytes, stream);
     if (st != TL_OK) return st;
     RaggedArgs r{nullptr, nullptr, a_off, A, b_off, b, x, piv_off, ipiv, info};
-    return ragged_solve(h, batch, n, r, static_cast<int32_t *>(h->ws), stream);
+    r.refine = mixed ? refine_steps : nullptr;
+    return ragged_solve(h, batch, n, r, static_cast<int32_t *>(h->ws), stream, mixed);
 }
