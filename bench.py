@@ -340,6 +340,113 @@ def newton_bench(tl, h, steps, warmup, torch, device, I, seed, npoints=NEWTON_PO
 
 
 # ---------------------------------------------------------------------------
+# ragged batch, binary64 vs binary32 factor + binary64 refinement
+# ---------------------------------------------------------------------------
+
+RAGGED_N = (6, 7, 12, 13, 19, 25, 32)
+RAGGED_W = (0.2, 0.25, 0.15, 0.15, 0.1, 0.1, 0.05)
+RAGGED_BATCH = 1 << 20
+
+
+def make_ragged_torch(batch, seed, device, torch, I):
+    """2^20 systems with n drawn from RAGGED_N (weights RAGGED_W); each n's
+    systems follow the sweep recipe (half U[-1,1], half kappa in [1e2,1e8],
+    b = A x_true), stored per system column-major one after another in
+    system order (so sizes are mixed in memory)."""
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    w = torch.tensor(RAGGED_W, dtype=torch.float64, device=device)
+    pick = torch.multinomial(w, batch, replacement=True, generator=g)
+    sizes = torch.tensor(RAGGED_N, dtype=torch.int64, device=device)[pick]
+    nn2 = sizes * sizes
+    a_off = torch.cumsum(nn2, 0) - nn2
+    b_off = torch.cumsum(sizes, 0) - sizes
+    Abuf = torch.empty(int(nn2.sum().item()), dtype=torch.float64, device=device)
+    bbuf = torch.empty(int(sizes.sum().item()), dtype=torch.float64, device=device)
+    xtrue = torch.empty_like(bbuf)
+    buckets = {}
+    for n in RAGGED_N:
+        idx = torch.nonzero(sizes == n).flatten()
+        if idx.numel() == 0:
+            continue
+        A, b, x = I.sweep_systems_torch(n, idx.numel(), seed * 1000 + n, device)
+        ia = (a_off[idx][:, None] + torch.arange(n * n, device=device)[None, :]).flatten()
+        ib = (b_off[idx][:, None] + torch.arange(n, device=device)[None, :]).flatten()
+        Abuf[ia] = A.transpose(1, 2).reshape(-1)
+        bbuf[ib] = b.reshape(-1)
+        xtrue[ib] = x.reshape(-1)
+        buckets[n] = (idx, ia, ib)
+        del A, b, x
+    return dict(sizes=sizes.to(torch.int32), a_off=a_off, b_off=b_off, A=Abuf, b=bbuf, xtrue=xtrue,
+                buckets=buckets, batch=batch)
+
+
+def ragged_errors(d, x, torch):
+    """Worst normwise backward error (in units of n * eps) and forward error
+    against x_true (relative, inf-norm) over all systems solved (info 0)."""
+    eps = 2.0 ** -52
+    be_max, fe_max = 0.0, 0.0
+    for n, (idx, ia, ib) in d["buckets"].items():
+        A = d["A"][ia].reshape(-1, n, n).transpose(1, 2)
+        xs = x[ib].reshape(-1, n)
+        r = d["b"][ib].reshape(-1, n) - torch.matmul(A, xs[:, :, None])[:, :, 0]
+        den = A.abs().sum(dim=2).amax(dim=1) * xs.abs().amax(dim=1) * eps * n
+        ok = torch.isfinite(xs).all(dim=1)
+        be = (r.abs().amax(dim=1) / den)[ok]
+        xt = d["xtrue"][ib].reshape(-1, n)
+        fe = ((xs - xt).abs().amax(dim=1) / xt.abs().amax(dim=1))[ok]
+        be_max = max(be_max, float(be.max().item()) if be.numel() else 0.0)
+        fe_max = max(fe_max, float(fe.max().item()) if fe.numel() else 0.0)
+    return be_max, fe_max
+
+
+def ragged_bench(tl, h, steps, warmup, torch, device, I, seed, batch=RAGGED_BATCH):
+    """One tl_lupp_solve_batched call over the mixed-size batch, binary64
+    and binary32-factor + binary64-refinement, each timed on its own."""
+    d = make_ragged_torch(batch, seed, device, torch, I)
+    x = torch.empty_like(d["b"])
+    ipiv = torch.empty(d["b"].numel(), dtype=torch.int32, device=device)
+    info = torch.empty(batch, dtype=torch.int32, device=device)
+    ref = torch.empty(batch, dtype=torch.int32, device=device)
+    stream = torch.cuda.current_stream()
+    out = {"workload": "2^20 systems, n in {6,7,12,13,19,25,32} with weights {.2,.25,.15,.15,.1,.1,.05}, "
+                       "half U[-1,1], half kappa in [1e2,1e8], b = A x_true; per-system column-major, sizes "
+                       "mixed in memory; one tl_lupp_solve_batched call",
+           "bytes_A": d["A"].numel() * 8}
+    for name, prec in (("fp64", tl.TL_PREC_FP64), ("fp32_ir", tl.TL_PREC_FP32_IR)):
+        def run():
+            st = tl.tl_lupp_solve_batched(h, batch, d["sizes"], d["a_off"], d["A"], d["b_off"], d["b"], x,
+                                          d["b_off"], ipiv, info, prec, ref if prec else None,
+                                          stream.cuda_stream)
+            if st != 0:
+                tl.check("tl_lupp_solve_batched", st, h)
+        for _ in range(warmup):
+            run()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ms = []
+        for _ in range(steps):
+            e0.record(stream)
+            run()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        med = statistics.median(ms)
+        be, fe = ragged_errors(d, x, torch)
+        out[name] = {"ms": med, "solves_per_s": batch / (med / 1e3), "max_backward_error_n_eps": be,
+                     "max_forward_error_vs_x_true": fe,
+                     "info_nonzero": int((info != 0).sum().item())}
+        if prec:
+            hist = torch.bincount((ref + 1).to(torch.int64), minlength=5).tolist()
+            out[name]["refine_steps_hist"] = {"fallback": hist[0], "0": hist[1], "1": hist[2], "2": hist[3],
+                                              "3": hist[4]}
+    out["fp32_ir_speedup"] = out["fp64"]["ms"] / out["fp32_ir"]["ms"]
+    del d
+    return out
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
@@ -416,6 +523,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-newton", action="store_true")
+    ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--batch", type=int, default=None,
                     help="cap on systems per n (small cases for profiling; the default is the full sweep)")
@@ -514,6 +622,13 @@ def main():
         log("newton")
         extra["newton"] = newton_bench(tl, h, max(2, args.steps // 2), 2, torch, device, I, rank_seed(1237, rank))
         extra["newton"]["points_per_s"] *= world
+        torch.cuda.empty_cache()
+
+    if not args.no_ragged:
+        log("ragged batch, binary64 and mixed precision")
+        extra["ragged"] = ragged_bench(tl, h, max(2, args.steps // 2), 2, torch, device, I, rank_seed(1238, rank))
+        for k in ("fp64", "fp32_ir"):
+            extra["ragged"][k]["solves_per_s"] *= world
         torch.cuda.empty_cache()
 
     e2e = None

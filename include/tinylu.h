@@ -168,18 +168,31 @@ tl_status tl_gesv_batched(tl_handle *h, int n, const double *A, double *LU_out, 
  *   b_off   device int64[batch]: b_s at b + b_off[s] and x_s at x + b_off[s]
  *   piv_off device int64[batch]: ipiv_s at ipiv + piv_off[s]
  *   info    device int32[batch]
- *   prec    TL_PREC_FP64 (factor in binary64), or TL_PREC_FP32_IR (factor
- *           in binary32, refine residual and correction in binary64; see
- *           refine_steps)
- *   refine_steps  nullable device int32[batch]: refinement steps taken
- *           (FP32_IR), -1 when the system fell back to a binary64 factor.
+ *   prec    TL_PREC_FP64: binary64 LUpp of every system.
+ *           TL_PREC_FP32_IR: mixed precision (iterative refinement, Langou
+ *           et al. 2006; the paper factors in binary64 only): factor a
+ *           binary32 copy of A_s, x = solve(b) in binary32, then up to 3
+ *           corrections x += solve(r) with the residual r = b - A x formed
+ *           in binary64, stopping once max|r_i| <= max|x_i| * ||A32||_inf *
+ *           sqrt(n) * 2^-53 (a binary64 backward error).  ipiv then holds
+ *           the binary32 pivots and info[s] = 0.  A system whose binary32
+ *           copy is out of range, whose binary32 factor meets a pivot
+ *           outside [FLT_MIN, Inf), whose solves overflow or whose residual
+ *           has not met the test after 3 corrections is solved by the
+ *           binary64 LUpp instead (x, ipiv and info exactly as with
+ *           TL_PREC_FP64).
+ *   refine_steps  nullable device int32[batch], TL_PREC_FP32_IR only (not
+ *           written with TL_PREC_FP64): corrections applied (0..3), or -1
+ *           when the system was solved in binary64 (fallback or n[s]
+ *           invalid).
  * info[s] = -2 when n[s] is outside 1..32 (that system is skipped, its x
  * and ipiv are not written); otherwise as for tl_gesv_batched.
  * Systems are bucketed by n on the device in the handle's workspace (grown
  * on demand with cudaMalloc; a call that would need to grow it while the
- * stream is being captured returns TL_ERR_NO_MEMORY) and solved by the
- * per-n kernels of tl_gesv_batched, one persistent launch per n.  batch must
- * be below 2^31.  TL_PREC_FP32_IR returns TL_ERR_UNSUPPORTED in this build.
+ * stream is being captured returns TL_ERR_NO_MEMORY; 4 bytes per system,
+ * 8 with TL_PREC_FP32_IR) and solved by per-n persistent launches; with
+ * TL_PREC_FP32_IR the systems handed back go through the binary64 kernels
+ * afterwards.  No host synchronization.  batch must be below 2^31.
  */
 tl_status tl_lupp_solve_batched(tl_handle *h, int64_t batch, const int32_t *n, const int64_t *a_off,
                                 const double *A, const int64_t *b_off, const double *b, double *x,
@@ -289,6 +302,100 @@ tl_status tl_autotune(tl_handle *h, int n_min, int n_max, tl_layout layout,
  */
 tl_status tl_dispatch_set(tl_handle *h, int n, tl_layout layout, int variant, int block);
 tl_status tl_dispatch_get(tl_handle *h, int n, tl_layout layout, int *variant, int *block);
+
+/*
+ * Request server: continuous batching of Newton-integration and
+ * standalone-solve requests on one device.  The paper integrates one batch
+ * of points per call (Algorithm 2); the server keeps a request loop on the
+ * host (a native thread owned by the server) that admits requests as they
+ * arrive against a device memory budget, and batches every admitted request
+ * into "ticks": one tick copies its requests' inputs into the server's
+ * device arena, launches one fused Newton kernel per law class over the
+ * concatenated points of all its requests (a job table: every point keeps
+ * its own request's arrays and parameters) and one ragged LUpp over all its
+ * solve systems, and copies the results back.  Up to `slots` ticks are in
+ * flight on their own streams, so requests that arrive while others run are
+ * admitted as soon as a slot and arena room free up, and their work overlaps
+ * on the device.  A point's or system's arithmetic does not depend on the
+ * other work in its tick: every result equals the one tl_newton_integrate
+ * (tl_lupp_solve_batched, TL_PREC_FP64) gives for the request alone.
+ */
+typedef struct tl_server tl_server;
+
+typedef enum { TL_REQ_NEWTON = 0, TL_REQ_SOLVE = 1 } tl_request_kind;
+
+/*
+ * One request.  Every pointer is a HOST pointer (page-locked memory gives
+ * asynchronous copies); the caller keeps the arrays valid and unmodified
+ * until the request is reported done.
+ *   TL_REQ_NEWTON: law, count = points; in = law fields and x, aux (Norton
+ *     stress, nullable), i1 = iterations, i2 = status, all as the arguments
+ *     of tl_newton_integrate (field-major with stride count).
+ *   TL_REQ_SOLVE: n (1..32), count = systems; in = A (per system
+ *     column-major, n*n doubles each), rhs = b (n each), x = solutions (n
+ *     each), i1 = ipiv (n each), i2 = info (one each), as
+ *     tl_lupp_solve_batched with TL_PREC_FP64 and consecutive systems.
+ */
+typedef struct {
+    int32_t kind;
+    int32_t n;
+    tl_law law;
+    int64_t count;
+    const double *in;
+    const double *rhs;
+    double *x;
+    double *aux;
+    int32_t *i1;
+    int32_t *i2;
+} tl_request;
+
+/*
+ * Server configuration.
+ *   budget_bytes        device arena holding every admitted request's
+ *                       buffers and each tick's tables (one cudaMalloc at
+ *                       creation).  A request that could never fit is
+ *                       refused at submission with TL_ERR_NO_MEMORY.
+ *   slots               ticks in flight at once (1..16), one stream each.
+ *   max_points_per_tick admission cap per tick (points + systems; a single
+ *                       larger request still forms a tick on its own);
+ *                       0 = one request per tick (plain per-request launches
+ *                       in arrival order, the comparator of batching).
+ *   rtol, max_iter      Newton stopping test of every Newton request.
+ */
+typedef struct {
+    size_t budget_bytes;
+    int32_t slots;
+    int64_t max_points_per_tick;
+    double rtol;
+    int32_t max_iter;
+} tl_server_config;
+
+typedef struct {
+    int64_t submitted;
+    int64_t completed;
+    int64_t failed;
+    int64_t ticks;
+    int64_t points;       /* Newton points + solve systems completed */
+    size_t arena_high_water;
+} tl_server_stats;
+
+/* Create a server on the handle's device (the handle must outlive it). */
+tl_status tl_server_create(tl_handle *h, const tl_server_config *cfg, tl_server **out);
+/* Queue a request (the descriptor is copied); *id identifies it.  Invalid
+ * descriptors return TL_ERR_INVALID_ARG (tl_last_bad_arg of the server's
+ * handle is not set), requests larger than the arena TL_ERR_NO_MEMORY. */
+tl_status tl_server_submit(tl_server *s, const tl_request *req, int64_t *id);
+/* Non-blocking: *done = 1 once the request's results are in its host
+ * arrays; then *req_status is its outcome (TL_OK or the error of its tick)
+ * and *latency_s the time from submission to completion.  An id reported
+ * done is released (later calls return TL_ERR_INVALID_ARG). */
+tl_status tl_server_test(tl_server *s, int64_t id, int32_t *done, int32_t *req_status, double *latency_s);
+/* Block until the request is done or timeout_s passes (TL_ERR_TIMEOUT, the
+ * request stays queued or running). */
+tl_status tl_server_wait(tl_server *s, int64_t id, double timeout_s, int32_t *req_status, double *latency_s);
+tl_status tl_server_stats_get(tl_server *s, tl_server_stats *out);
+/* Finish every queued request, stop the request loop, free the arena. */
+tl_status tl_server_destroy(tl_server *s);
 
 #ifdef __cplusplus
 }
