@@ -19,6 +19,8 @@ Linear Systems on GPUs: Application to Constitutive Laws"):
   * norton_eval -- the Norton law of Sec. 4.3 (equations not printed in the
     paper; standard implicit J2 + Norton form in Mandel notation).
   * tanh_eval -- synthetic law F(x) = A x + c*tanh(x) - b.
+  * norton_tangent -- consistent tangent operator at a converged state
+    (Sec. 4.3, the multi-right-hand-side solve after convergence).
   * sgetrf / ir_gesv -- binary32 factorization and binary64 iterative
     refinement (not in the paper: the published scheme of Langou et al.
     2006, as LAPACK's dsgesv, with every operation's format and order
@@ -63,6 +65,8 @@ def _declare(lib):
     lib.orc_sgetrf.argtypes = [C.c_int, C.POINTER(C.c_float), _i32]
     lib.orc_ir_gesv_batch.restype = None
     lib.orc_ir_gesv_batch.argtypes = [C.c_int, C.c_int64, _d, _d, _d, _i32, _i32, _i32, C.c_int]
+    lib.orc_norton_tangent.restype = C.c_int
+    lib.orc_norton_tangent.argtypes = [_d, _d, _d, _d, _d]
     lib.orc_norton_eval.restype = None
     lib.orc_norton_eval.argtypes = [_d, _d, _d, _d, _d, _d, _d]
     lib.orc_tanh_eval.restype = None
@@ -199,6 +203,20 @@ def norton_eval(prm, sig0, deps, x, lib=None):
     sig = np.empty(6)
     lib.orc_norton_eval(_ptr(prm), _ptr(sig0), _ptr(deps), _ptr(x), _ptr(F), _ptr(Jcm), _ptr(sig))
     return F, Jcm.reshape(7, 7).T.copy(), sig
+
+
+def norton_tangent(prm, sig0, deps, x, lib=None):
+    """Consistent tangent dsig/ddeps (6x6, math-indexed) of the Norton law
+    at the converged state x of one point (Sec. 4.3), and the info of the
+    Jacobian's factorization."""
+    lib = lib or load()
+    prm = np.ascontiguousarray(prm, np.float64)
+    sig0 = np.ascontiguousarray(sig0, np.float64)
+    deps = np.ascontiguousarray(deps, np.float64)
+    x = np.ascontiguousarray(x, np.float64)
+    Dcm = np.empty(36)
+    info = lib.orc_norton_tangent(_ptr(prm), _ptr(sig0), _ptr(deps), _ptr(x), _ptr(Dcm))
+    return Dcm.reshape(6, 6).T.copy(), info
 
 
 def tanh_eval(A, c, b, x, lib=None):

@@ -29,6 +29,9 @@
  *                  Norton form is used, see the module docstring of the
  *                  Python wrapper for the reading).
  *   orc_tanh_eval -- synthetic law F(x) = A x + c .* tanh(x) - b.
+ *   orc_norton_tangent -- consistent tangent of the Norton law at a
+ *                  converged state (Sec. 4.3, the multi-RHS solve after
+ *                  convergence).
  *   orc_sgetrf / orc_sgetrs / orc_ir_solve -- binary32 factorization with
  *                  binary64 iterative refinement (not in the paper; the
  *                  published scheme of Langou et al. 2006, see below).
@@ -619,6 +622,39 @@ static void tanh_eval_cb(const void *cc, const double *x, double *F, double *J)
 {
     const tanh_ctx *ctx = (const tanh_ctx *)cc;
     orc_tanh_eval(ctx->n, ctx->A, ctx->c, ctx->b, x, F, J);
+}
+
+/*
+ * orc_norton_tangent: consistent tangent operator of the implicit Norton
+ * law at a converged state x (Sec. 4.3: one multi-right-hand-side solve
+ * after convergence).  Differentiating F(x(deps); deps) = 0 gives
+ * J dx/ddeps = -dF/ddeps = [I_6; 0] (f_el = de_el - deps + dp n, f_p does
+ * not involve deps), so X = J^{-1} [I_6; 0] (7x6, six solves with the
+ * factors of one orc_getrf) and dsig/ddeps = C X[0..5][.], with the Mandel
+ * elasticity C = lambda 1 (x) 1 + 2 mu I.  D receives the 6x6 tangent
+ * column-major (D[i + 6 j] = dsig_i / ddeps_j).  Returns the info of the
+ * factorization (D is NaN when it is not 0).
+ */
+int orc_norton_tangent(const double *prm, const double *sig0, const double *deps, const double *x, double *D)
+{
+    const double E = prm[0], nu = prm[1];
+    const double lambda = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    const double mu = E / (2.0 * (1.0 + nu));
+    double F[7], J[49], X[7];
+    int32_t piv[7];
+    orc_norton_eval(prm, sig0, deps, x, F, J, NULL);
+    int info = orc_getrf(7, J, piv, NULL);
+    if (info != 0) {
+        for (int i = 0; i < 36; ++i) D[i] = NAN;
+        return info;
+    }
+    for (int j = 0; j < 6; ++j) {
+        for (int i = 0; i < 7; ++i) X[i] = (i == j) ? 1.0 : 0.0;
+        orc_getrs(7, J, piv, X);
+        const double tr = X[0] + X[1] + X[2];
+        for (int i = 0; i < 6; ++i) D[i + 6 * j] = 2.0 * mu * X[i] + (i < 3 ? lambda * tr : 0.0);
+    }
+    return 0;
 }
 
 /*

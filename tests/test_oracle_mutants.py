@@ -21,7 +21,7 @@ from oracle import build as obuild
 from paper_2609_15217_gb300 import inputs
 
 from test_oracle_ir import IR_PINS
-from test_oracle_newton import radial_return
+from test_oracle_newton import pin_tangent, radial_return
 
 EPS = np.finfo(np.float64).eps
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "lupp_hand_examples.json")
@@ -50,10 +50,15 @@ MUTATIONS = {
                              "J[i + 7 * j] = (i == j ? 1.0 : 0.0) - c * v;"),
     "norton_power_off_by_one": ("for (int i = 0; i < m - 1; ++i) pw_m1 = pw_m1 * seq;",
                                 "for (int i = 0; i < m - 2; ++i) pw_m1 = pw_m1 * seq;"),
-    "norton_shear_modulus": ("const double mu = E / (2.0 * (1.0 + nu));", "const double mu = E / (1.0 + nu);"),
+    "norton_shear_modulus": ("const int m = (int)prm[3];\n    const double lambda = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));\n    const double mu = E / (2.0 * (1.0 + nu));",
+                             "const int m = (int)prm[3];\n    const double lambda = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));\n    const double mu = E / (1.0 + nu);"),
     "newton_absolute_test": ("if (r <= rtol * r0 || r0 == 0.0)", "if (r <= rtol || r0 == 0.0)"),
     "newton_counts_evals": ("        ++k;\n        eval(ctx, x, F, J);", "        k += 2;\n        eval(ctx, x, F, J);"),
     "tanh_jacobian_sign": ("c[i] * (1.0 - t * t)", "c[i] * (1.0 + t * t)"),
+    "tangent_rhs_sign": ("for (int i = 0; i < 7; ++i) X[i] = (i == j) ? 1.0 : 0.0;",
+                         "for (int i = 0; i < 7; ++i) X[i] = (i == j) ? -1.0 : 0.0;"),
+    "tangent_drops_lambda": ("D[i + 6 * j] = 2.0 * mu * X[i] + (i < 3 ? lambda * tr : 0.0);",
+                             "D[i + 6 * j] = 2.0 * mu * X[i];"),
     "ir_tie_break_last": ("return fabsf(a) > fabsf(b);", "return fabsf(a) >= fabsf(b);"),
     "ir_l_part_not_swapped": ("for (int j = 0; j < n; ++j) {\n                float t = AT(a, n, k, j);",
                               "for (int j = k; j < n; ++j) {\n                float t = AT(a, n, k, j);"),
@@ -166,7 +171,7 @@ def pin_tanh(lib):
         assert np.array_equal(r1["x"], r2["x"])
 
 
-PINS = [pin_golden, pin_reconstruction_and_errors, pin_singular, pin_norton, pin_tanh, *IR_PINS]
+PINS = [pin_golden, pin_reconstruction_and_errors, pin_singular, pin_norton, pin_tanh, pin_tangent, *IR_PINS]
 
 
 def failing_pins(lib):

@@ -234,3 +234,52 @@ def test_relative_stop_is_scale_invariant():
             assert np.array_equal(r1["iterations"], r2["iterations"])
             assert np.array_equal(r1["status"], r2["status"])
             assert np.array_equal(r1["x"], r2["x"])
+
+
+# ---------------------------------------------------------------------------
+# Consistent tangent operator (Sec. 4.3: the multi-RHS solve after
+# convergence)
+# ---------------------------------------------------------------------------
+
+def _mandel_C(prm):
+    E, nu = prm[0], prm[1]
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    mu = E / (2 * (1 + nu))
+    C = 2 * mu * np.eye(6)
+    C[:3, :3] += lam
+    return C
+
+
+def pin_tangent(lib=None):
+    prm = oracle.norton_params()
+    sig0, deps = inputs.norton_points(12, 4321)
+    # elastic step: the tangent is the elasticity tensor exactly
+    prm0 = oracle.norton_params(A=0.0)
+    r = oracle.newton_norton(prm0, sig0, deps, lib=lib)
+    for p in range(4):
+        D, info = oracle.norton_tangent(prm0, sig0[p], deps[p], r["x"][p], lib=lib)
+        assert info == 0 and np.array_equal(D, _mandel_C(prm0))
+    r = oracle.newton_norton(prm, sig0, deps, rtol=1e-14, max_iter=40, lib=lib)
+    assert (r["status"] == 0).all()
+    h = 1e-7
+    for p in range(6):
+        D, info = oracle.norton_tangent(prm, sig0[p], deps[p], r["x"][p], lib=lib)
+        assert info == 0
+        # associative J2 flow: the consistent tangent is symmetric
+        assert np.abs(D - D.T).max() <= 1e-9 * np.abs(D).max()
+        # softer than elasticity along the flow, never stiffer
+        assert np.linalg.eigvalsh(0.5 * (D + D.T)).max() <= np.linalg.eigvalsh(_mandel_C(prm)).max() * (1 + 1e-12)
+        # central differences of the converged stress in deps
+        Dfd = np.empty((6, 6))
+        for j in range(6):
+            dp_, dm_ = deps[p:p + 1].copy(), deps[p:p + 1].copy()
+            dp_[0, j] += h
+            dm_[0, j] -= h
+            sp = oracle.newton_norton(prm, sig0[p:p + 1], dp_, rtol=1e-15, max_iter=60, lib=lib)["sig"][0]
+            sm = oracle.newton_norton(prm, sig0[p:p + 1], dm_, rtol=1e-15, max_iter=60, lib=lib)["sig"][0]
+            Dfd[:, j] = (sp - sm) / (2 * h)
+        assert np.abs(D - Dfd).max() <= 1e-5 * np.abs(D).max(), np.abs(D - Dfd).max() / np.abs(D).max()
+
+
+def test_tangent_pins():
+    pin_tangent()
