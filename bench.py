@@ -447,6 +447,147 @@ def ragged_bench(tl, h, steps, warmup, torch, device, I, seed, batch=RAGGED_BATC
 
 
 # ---------------------------------------------------------------------------
+# served Newton stream (continuous batching vs plain per-request launches)
+# ---------------------------------------------------------------------------
+
+SERVE_TANH_N = (7, 13, 20, 32)
+SERVE_MAX_PTS = 1 << 16
+SERVE_BUDGET = 20 * (1 << 30)
+
+
+class ServeWorkload:
+    """Request classes of the served stream: 30% Norton n = 7 points (the
+    Newton workload), 70% tanh-law points with n uniform in {7, 13, 20, 32}
+    (A = nI + U[-1,1], c in U[0.5,2], b in U[-3,3] n); request sizes
+    log-uniform in [1k, 64k] points.  Inputs come from one page-locked pool
+    per class (requests read its first `count` points through ld_in);
+    outputs go to a ring of page-locked output slots."""
+
+    def __init__(self, tl, torch, I, seed, out_slots=96):
+        self.tl = tl
+        g = np.random.default_rng(seed)
+        self.pools = {}
+        P = SERVE_MAX_PTS
+        sig0, deps = I.norton_points(P, seed)
+        f = np.concatenate([sig0.T, deps.T], axis=0)
+        self.pools["norton"] = torch.from_numpy(np.ascontiguousarray(f)).pin_memory()
+        for n in SERVE_TANH_N:
+            A, c, b = I.tanh_points(n, P, seed + n)
+            f = np.concatenate([A.transpose(0, 2, 1).reshape(P, n * n).T, c.T, b.T], axis=0)
+            self.pools[n] = torch.from_numpy(np.ascontiguousarray(f)).pin_memory()
+            del A, c, b, f
+        self.laws = {"norton": tl.make_law(tl.TL_LAW_NORTON, 7, (200000.0, 0.3, 1e-12, 4.0, 1.0))}
+        for n in SERVE_TANH_N:
+            self.laws[n] = tl.make_law(tl.TL_LAW_TANH, n)
+        self.out = [dict(x=torch.empty(32 * P, dtype=torch.float64).pin_memory(),
+                         it=torch.empty(P, dtype=torch.int32).pin_memory(),
+                         st=torch.empty(P, dtype=torch.int32).pin_memory()) for _ in range(out_slots)]
+        self.g = g
+
+    def draw(self, count):
+        """count request descriptors: (class, points)."""
+        out = []
+        for _ in range(count):
+            cls = "norton" if self.g.random() < 0.3 else int(self.g.choice(SERVE_TANH_N))
+            pts = int(np.exp(self.g.uniform(np.log(1000), np.log(SERVE_MAX_PTS))))
+            out.append((cls, pts))
+        return out
+
+    def request(self, cls, pts, slot):
+        tl = self.tl
+        o = self.out[slot]
+        return tl.make_request(tl.TL_REQ_NEWTON, pts, self.pools[cls].data_ptr(), o["x"].data_ptr(),
+                               o["it"].data_ptr(), o["st"].data_ptr(), law=self.laws[cls], ld_in=SERVE_MAX_PTS)
+
+
+def run_stream(tl, h, wl, reqs, arrivals, mode):
+    """Submit reqs[i] at arrivals[i] seconds (None: all at once) to a server
+    in `mode` and wait for all.  Returns latencies, makespan and lags."""
+    cap, slots = (1 << 18, 4) if mode == "batched" else (0, 1)
+    st, srv = tl.tl_server_create(h, SERVE_BUDGET, slots, cap, 1e-10, 20)
+    tl.check("tl_server_create", st, h)
+    free_slots = list(range(len(wl.out)))
+    inflight = {}   # id -> (slot, descriptor, submission delay after the arrival)
+    lat, lag = [], []
+    t0 = time.perf_counter()
+
+    def reap(block=False):
+        for rid in list(inflight):
+            if block:
+                s2, rs, l = tl.tl_server_wait(srv, rid, 600.0)
+                done = 1
+            else:
+                s2, done, rs, l = tl.tl_server_test(srv, rid)
+            if s2 == 0 and done:
+                if rs != 0:
+                    raise RuntimeError(f"request failed: {rs}")
+                slot, _, delay = inflight.pop(rid)
+                lat.append(l + delay)     # latency counted from the arrival
+                free_slots.append(slot)
+
+    for i, (cls, pts) in enumerate(reqs):
+        due = t0 + (arrivals[i] if arrivals is not None else 0.0)
+        if arrivals is not None:
+            while True:
+                now = time.perf_counter()
+                if now >= due:
+                    break
+                if due - now > 0.0005:
+                    reap()
+                    time.sleep(min(0.0005, due - now - 0.0003))
+        while not free_slots:
+            reap()
+        slot = free_slots.pop()
+        req = wl.request(cls, pts, slot)
+        delay = max(0.0, time.perf_counter() - due) if arrivals is not None else 0.0
+        lag.append(delay)
+        s2, rid = tl.tl_server_submit(srv, req)
+        tl.check("tl_server_submit", s2, h)
+        inflight[rid] = (slot, req, delay)
+    reap(block=True)
+    makespan = time.perf_counter() - t0
+    _, stats = tl.tl_server_stats_get(srv)
+    tl.tl_server_destroy(srv)
+    return lat, makespan, lag, stats
+
+
+def serve_bench(tl, h, torch, I, seed, burst=160, seconds=3.0):
+    wl = ServeWorkload(tl, torch, I, seed)
+    out = {"workload": "served Newton stream: 30% Norton n=7, 70% tanh law n in {7,13,20,32}; request sizes "
+                       "log-uniform in [1k, 64k] points; Poisson arrivals; host page-locked inputs and outputs "
+                       "(H2D and D2H inside every request's latency); 20 GiB device arena",
+           "batched": {"slots": 4, "max_points_per_tick": 1 << 18}, "plain": {"slots": 1, "one_request_per_tick": True}}
+    # capacity: a burst of requests submitted at once
+    reqs = wl.draw(burst)
+    pts = sum(p for _, p in reqs)
+    for mode in ("batched", "plain"):
+        run_stream(tl, h, wl, reqs[:8], None, mode)   # warm-up
+        lat, span, _, stats = run_stream(tl, h, wl, reqs, None, mode)
+        out[mode]["capacity_points_per_s"] = pts / span
+        out[mode]["capacity_requests_per_s"] = burst / span
+        out[mode]["ticks_in_burst"] = stats["ticks"]
+    cap_rps = out["batched"]["capacity_requests_per_s"]
+    mean_pts = pts / burst
+    for load in (0.5, 0.8, 0.95):
+        rate = load * cap_rps
+        count = max(50, int(rate * seconds))
+        reqs = wl.draw(count)
+        arrivals = np.cumsum(wl.g.exponential(1.0 / rate, size=count))
+        for mode in ("batched", "plain"):
+            lat, span, lag, stats = run_stream(tl, h, wl, reqs, arrivals, mode)
+            lat_ms = np.array(lat) * 1e3
+            out[mode][f"load_{int(load * 100)}"] = {
+                "offered_requests_per_s": rate, "requests": count,
+                "points_per_s": sum(p for _, p in reqs) / span,
+                "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                "max_ms": float(lat_ms.max()), "ticks": stats["ticks"],
+                "submit_lag_p99_ms": float(np.percentile(np.array(lag) * 1e3, 99))}
+    out["mean_points_per_request"] = mean_pts
+    del wl
+    return out
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
@@ -524,6 +665,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-newton", action="store_true")
     ap.add_argument("--no-ragged", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--batch", type=int, default=None,
                     help="cap on systems per n (small cases for profiling; the default is the full sweep)")
@@ -629,6 +771,11 @@ def main():
         extra["ragged"] = ragged_bench(tl, h, max(2, args.steps // 2), 2, torch, device, I, rank_seed(1238, rank))
         for k in ("fp64", "fp32_ir"):
             extra["ragged"][k]["solves_per_s"] *= world
+        torch.cuda.empty_cache()
+
+    if not args.no_serve and world == 1:
+        log("served Newton stream")
+        extra["serve"] = serve_bench(tl, h, torch, I, rank_seed(1239, rank))
         torch.cuda.empty_cache()
 
     e2e = None

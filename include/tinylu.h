@@ -256,6 +256,24 @@ tl_status tl_newton_integrate(tl_handle *h, const tl_law *law, int64_t npoints,
                               cudaStream_t stream);
 
 /*
+ * tl_newton_integrate_tangent -- tl_newton_integrate for the Norton law that
+ * also returns, for every converged point, the consistent tangent operator
+ * dsig/ddeps (Sec. 4.3: one multi-right-hand-side solve after convergence):
+ * the converged Jacobian is factored once and solved for the six columns of
+ * [I_6; 0]; the strain rows are mapped to stress by the Mandel elasticity.
+ *   tangent  device double[36 * npoints]:
+ *            tangent[(i + 6 j) * npoints + p] = dsig_i / ddeps_j; NaN for
+ *            points that did not converge.
+ * Other arguments as tl_newton_integrate (tangent is argument 7; the
+ * arguments after it are numbered one higher).  TL_LAW_TANH returns
+ * TL_ERR_UNSUPPORTED.
+ */
+tl_status tl_newton_integrate_tangent(tl_handle *h, const tl_law *law, int64_t npoints,
+                                      const double *inputs, double *x, double *outputs, double *tangent,
+                                      int32_t *iterations, int32_t *status, double rtol, int max_iter,
+                                      cudaStream_t stream);
+
+/*
  * tl_newton_integrate_cpu_driven -- the batched, CPU-driven evaluation of
  * the same Newton problem (Algorithm 1; the comparator of the fused kernel,
  * Sec. 2.4): each iteration launches one kernel that assembles F and J for
@@ -330,7 +348,9 @@ typedef enum { TL_REQ_NEWTON = 0, TL_REQ_SOLVE = 1 } tl_request_kind;
  * until the request is reported done.
  *   TL_REQ_NEWTON: law, count = points; in = law fields and x, aux (Norton
  *     stress, nullable), i1 = iterations, i2 = status, all as the arguments
- *     of tl_newton_integrate (field-major with stride count).
+ *     of tl_newton_integrate (field-major with stride count), except that
+ *     the fields may have a larger stride ld_in (0 = count): field f of
+ *     point p at in[f*ld_in + p], so requests can share one input pool.
  *   TL_REQ_SOLVE: n (1..32), count = systems; in = A (per system
  *     column-major, n*n doubles each), rhs = b (n each), x = solutions (n
  *     each), i1 = ipiv (n each), i2 = info (one each), as
@@ -341,6 +361,7 @@ typedef struct {
     int32_t n;
     tl_law law;
     int64_t count;
+    int64_t ld_in;
     const double *in;
     const double *rhs;
     double *x;

@@ -76,10 +76,11 @@ bool law_params(const tl_law &law, NewtonJob *jb)
 
 using namespace tl;
 
-extern "C" tl_status tl_newton_integrate(tl_handle *h, const tl_law *law, int64_t npoints,
-                                         const double *inputs, double *x, double *outputs,
-                                         int32_t *iterations, int32_t *status, double rtol, int max_iter,
-                                         cudaStream_t stream)
+namespace {
+
+tl_status integrate(tl_handle *h, const tl_law *law, int64_t npoints, const double *inputs, double *x,
+                    double *outputs, double *tangent, int32_t *iterations, int32_t *status, double rtol,
+                    int max_iter, cudaStream_t stream)
 {
     if (!h) return TL_ERR_INVALID_ARG;
     h->last_bad_arg = 0;
@@ -99,6 +100,7 @@ extern "C" tl_status tl_newton_integrate(tl_handle *h, const tl_law *law, int64_
     B.one.in = inputs;
     B.one.x = x;
     B.one.out = law->id == TL_LAW_NORTON ? outputs : nullptr;
+    B.one.tangent = tangent;
     B.one.iters = iterations;
     B.one.status = status;
     B.one.npoints = npoints;
@@ -108,4 +110,27 @@ extern "C" tl_status tl_newton_integrate(tl_handle *h, const tl_law *law, int64_
     B.rtol = rtol;
     B.max_iter = max_iter;
     return newton_launch(h, law->id, law->n, B, stream);
+}
+
+}  // namespace
+
+extern "C" tl_status tl_newton_integrate(tl_handle *h, const tl_law *law, int64_t npoints,
+                                         const double *inputs, double *x, double *outputs,
+                                         int32_t *iterations, int32_t *status, double rtol, int max_iter,
+                                         cudaStream_t stream)
+{
+    return integrate(h, law, npoints, inputs, x, outputs, nullptr, iterations, status, rtol, max_iter, stream);
+}
+
+extern "C" tl_status tl_newton_integrate_tangent(tl_handle *h, const tl_law *law, int64_t npoints,
+                                                 const double *inputs, double *x, double *outputs, double *tangent,
+                                                 int32_t *iterations, int32_t *status, double rtol, int max_iter,
+                                                 cudaStream_t stream)
+{
+    if (!h) return TL_ERR_INVALID_ARG;
+    h->last_bad_arg = 0;
+    if (!law) return fail_arg(h, 2);
+    if (law->id != TL_LAW_NORTON) return TL_ERR_UNSUPPORTED;
+    if (npoints > 0 && (!tangent || (reinterpret_cast<uintptr_t>(tangent) & 7))) return fail_arg(h, 7);
+    return integrate(h, law, npoints, inputs, x, outputs, tangent, iterations, status, rtol, max_iter, stream);
 }

@@ -82,6 +82,41 @@ static __device__ __noinline__ Solve7 slow_norton_solve(NortonParams P, NortonSt
     return out;
 }
 
+// Consistent tangent at a converged state (Sec. 4.3: one multi-RHS solve
+// after convergence): J X = [I_6; 0] with the six right-hand sides carried
+// through one elimination, then dsig/ddeps = C X[0..5] (Mandel elasticity
+// C = lambda 1 (x) 1 + 2 mu I).  Stores tangent[(i + 6 j) np + p]; NaN when
+// the Jacobian is singular or not finite.  Out of line: it runs once per
+// point and must not weigh on the Newton loop's registers.
+static __device__ __noinline__ void norton_tangent_store(NortonParams P, NortonState st, double *tangent, int64_t np,
+                                                         int64_t p)
+{
+    double F[7], J[7][7], sig[6], X[6][7];
+    norton_eval(P, st.sig0, st.deps, st.x, F, J, sig);
+    const bool bad = dev::any_nonfinite<7>(J);
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int i = 0; i < 7; ++i) X[c][i] = (i == c) ? 1.0 : 0.0;
+    int piv[7];
+    double rcp[7];
+    bool tiny = false;
+    const int info = dev::lu_thread_factor<7, false, 6>(J, X, piv, rcp, tiny);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) dev::lu_thread_backsolve<7>(J, X[c], rcp, tiny);
+    const bool ok = info == 0 && !bad;
+    const double two_mu = 2.0 * P.mu;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const double tr = X[j][0] + X[j][1] + X[j][2];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const double d = (i < 3) ? fma(P.lambda, tr, two_mu * X[j][i]) : two_mu * X[j][i];
+            tangent[(i + 6 * j) * np + p] = ok ? d : dev::nan_value();
+        }
+    }
+}
+
 static __global__ void __launch_bounds__(128) k_newton_norton(NewtonBatch B)
 {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -150,6 +185,21 @@ static __global__ void __launch_bounds__(128) k_newton_norton(NewtonBatch B)
         if (jb.out) {
 #pragma unroll
             for (int i = 0; i < 6; ++i) jb.out[i * np + p] = sig[i];
+        }
+        if (jb.tangent) {
+            if (st == TL_NEWTON_CONVERGED) {
+                NortonState ns;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    ns.sig0[i] = sig0[i];
+                    ns.deps[i] = deps[i];
+                }
+#pragma unroll
+                for (int i = 0; i < 7; ++i) ns.x[i] = x[i];
+                norton_tangent_store(P, ns, jb.tangent, np, p);
+            } else {
+                for (int i = 0; i < 36; ++i) jb.tangent[i * np + p] = dev::nan_value();
+            }
         }
         jb.iters[p] = k;
         jb.status[p] = st;

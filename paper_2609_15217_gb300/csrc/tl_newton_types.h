@@ -15,6 +15,7 @@ struct NewtonJob {
     const double *in;
     double *x;
     double *out;  // nullable (Norton: end-of-step stress)
+    double *tangent;  // nullable (Norton: consistent tangent, 36 rows)
     int32_t *iters;
     int32_t *status;
     int64_t npoints;

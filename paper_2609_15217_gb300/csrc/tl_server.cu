@@ -1,0 +1,540 @@
+// tl_server.cu -- the request server of tinylu.h: a native request loop
+// (one host thread per server) doing continuous batching of Newton and
+// solve requests on one device.
+//
+// Life of a request: submit (descriptor copied, queued FIFO) -> admitted
+// into a tick when a slot (stream) is free and the arena has room -> its
+// inputs copied into its arena block, its points integrated by the fused
+// Newton kernel of its law class (one launch per class over every request of
+// the tick, through a job table) or its systems solved by one ragged LUpp
+// over every solve of the tick -> results copied back to its host arrays ->
+// done when the tick's event completes (its arena block is released then).
+// Ticks on different slots overlap on the device; requests that arrive while
+// ticks run wait at most until a slot frees up.
+//
+// There are no device-side waits: the request loop lives on the host, so a
+// kernel never spins on a flag the host writes.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "tinylu.h"
+#include "tl_arena.h"
+#include "tl_handle.h"
+#include "tl_internal.h"
+#include "tl_newton_types.h"
+
+namespace tl {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+constexpr int kMaxSlots = 16;
+constexpr size_t kMaxJobsPerTick = 4096;
+
+size_t up(size_t b) { return Arena::round_up(b); }
+
+struct Req {
+    int64_t id = 0;
+    tl_request d{};
+    NewtonJob job{};  // law parameters (Newton)
+    Clock::time_point t_submit, t_done;
+    bool done = false;
+    int32_t status = TL_OK;
+    size_t off = SIZE_MAX, bytes = 0;   // arena block
+    size_t o_in = 0, o_x = 0, o_aux = 0, o_i1 = 0, o_i2 = 0;  // offsets inside the arena
+    int fields() const { return d.law.id == TL_LAW_NORTON ? 12 : d.law.n * d.law.n + 2 * d.law.n; }
+    int xrows() const { return d.law.id == TL_LAW_NORTON ? 7 : d.law.n; }
+    bool has_aux() const { return d.kind == TL_REQ_NEWTON && d.law.id == TL_LAW_NORTON && d.aux; }
+    // arena layout of the request's own buffers
+    size_t layout(size_t base)
+    {
+        size_t o = base;
+        const size_t c = static_cast<size_t>(d.count);
+        if (d.kind == TL_REQ_NEWTON) {
+            o_in = o; o += up(c * fields() * 8);
+            o_x = o; o += up(c * xrows() * 8);
+            o_aux = o; o += has_aux() ? up(c * 6 * 8) : 0;
+            o_i1 = o; o += up(c * 4);
+            o_i2 = o; o += up(c * 4);
+        } else {
+            const size_t n = static_cast<size_t>(d.n);
+            o_in = o; o += up(c * n * n * 8);
+            o_x = o; o += up(c * n * 8);   // b copied here, solved in place
+            o_i1 = o; o += up(c * n * 4);
+        }
+        return o - base;
+    }
+    // tick-table bytes this request adds (job entry, or ragged arrays)
+    size_t table_bytes() const
+    {
+        return d.kind == TL_REQ_NEWTON ? sizeof(NewtonJob) : static_cast<size_t>(d.count) * 32;
+    }
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    tl_handle *h = nullptr;  // own handle: the ragged solve's workspace is per handle
+    bool busy = false;
+    std::vector<Req *> reqs;
+    size_t scratch_off = SIZE_MAX, scratch_bytes = 0;
+    char *stage = nullptr;  // page-locked staging of the tick tables
+    size_t stage_bytes = 0;
+};
+
+}  // namespace
+}  // namespace tl
+
+using namespace tl;
+
+struct tl_server {
+    tl_handle *h = nullptr;
+    int device = 0;
+    tl_server_config cfg{};
+    char *base = nullptr;
+    Arena arena;
+    std::vector<Slot> slots;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Req *> pending;
+    std::unordered_map<int64_t, Req *> reqs;
+    int64_t next_id = 1;
+    bool stop = false;
+    tl_server_stats stats{};
+    std::thread loop;
+
+    void run();
+    bool form_tick(Slot &sl, std::vector<Req *> &batch, size_t &scratch_off, size_t &scratch_bytes);
+    tl_status enqueue(Slot &sl, std::vector<Req *> &batch);
+    void finish(Slot &sl, int32_t status);
+};
+
+namespace {
+
+tl_status check_request(const tl_request *r)
+{
+    if (!r) return TL_ERR_INVALID_ARG;
+    if (r->count < 0) return TL_ERR_INVALID_ARG;
+    if (r->kind == TL_REQ_NEWTON) {
+        NewtonJob jb{};
+        if (!law_params(r->law, &jb)) return TL_ERR_INVALID_ARG;
+        if (r->count > 0 && (!r->in || !r->x || !r->i1 || !r->i2)) return TL_ERR_INVALID_ARG;
+        if (r->ld_in != 0 && r->ld_in < r->count) return TL_ERR_INVALID_ARG;
+        return TL_OK;
+    }
+    if (r->kind == TL_REQ_SOLVE) {
+        if (r->n < 1 || r->n > TL_MAX_N) return TL_ERR_INVALID_ARG;
+        if (r->count > 0 && (!r->in || !r->rhs || !r->x || !r->i1 || !r->i2)) return TL_ERR_INVALID_ARG;
+        return TL_OK;
+    }
+    return TL_ERR_INVALID_ARG;
+}
+
+tl_status grow_stage(Slot &sl, size_t bytes)
+{
+    if (sl.stage_bytes >= bytes) return TL_OK;
+    if (sl.stage) cudaFreeHost(sl.stage);
+    sl.stage = nullptr;
+    sl.stage_bytes = 0;
+    const size_t want = std::max(bytes, static_cast<size_t>(1) << 20);
+    if (cudaHostAlloc(reinterpret_cast<void **>(&sl.stage), want, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        sl.stage = nullptr;
+        return TL_ERR_NO_MEMORY;
+    }
+    sl.stage_bytes = want;
+    return TL_OK;
+}
+
+}  // namespace
+
+// Called with mu held: take requests from the head of the queue while the
+// tick cap and the arena allow, and place the tick's table scratch.
+bool tl_server::form_tick(Slot &, std::vector<Req *> &batch, size_t &scratch_off, size_t &scratch_bytes)
+{
+    const int64_t cap = cfg.max_points_per_tick;
+    int64_t pts = 0;
+    size_t table = 0;
+    while (!pending.empty() && batch.size() < kMaxJobsPerTick) {
+        Req *r = pending.front();
+        if (!batch.empty() && (cap == 0 || pts + r->d.count > cap)) break;
+        const size_t off = arena.alloc(r->bytes);
+        if (off == SIZE_MAX) break;
+        r->off = off;
+        r->layout(off);
+        batch.push_back(r);
+        pending.pop_front();
+        pts += r->d.count;
+        table += up(r->table_bytes());
+    }
+    while (!batch.empty()) {
+        scratch_bytes = table + 4 * Arena::kAlign;
+        scratch_off = arena.alloc(scratch_bytes);
+        if (scratch_off != SIZE_MAX) return true;
+        Req *r = batch.back();  // give the last request back and retry
+        batch.pop_back();
+        arena.release(r->off, r->bytes);
+        r->off = SIZE_MAX;
+        table -= up(r->table_bytes());
+        pending.push_front(r);
+    }
+    return false;
+}
+
+// Issue a tick's copies and kernels on the slot's stream (no lock held).
+tl_status tl_server::enqueue(Slot &sl, std::vector<Req *> &batch)
+{
+    cudaStream_t st = sl.stream;
+    cudaError_t e = cudaSuccess;
+    auto dptr = [&](size_t off) { return base + off; };
+    // inputs
+    for (Req *r : batch) {
+        const size_t c = static_cast<size_t>(r->d.count);
+        if (c == 0) continue;
+        if (r->d.kind == TL_REQ_NEWTON) {
+            const size_t ld = r->d.ld_in > 0 ? static_cast<size_t>(r->d.ld_in) : c;
+            if (ld == c)
+                e = cudaMemcpyAsync(dptr(r->o_in), r->d.in, c * r->fields() * 8, cudaMemcpyHostToDevice, st);
+            else
+                e = cudaMemcpy2DAsync(dptr(r->o_in), c * 8, r->d.in, ld * 8, c * 8, static_cast<size_t>(r->fields()),
+                                      cudaMemcpyHostToDevice, st);
+        } else {
+            const size_t n = static_cast<size_t>(r->d.n);
+            e = cudaMemcpyAsync(dptr(r->o_in), r->d.in, c * n * n * 8, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dptr(r->o_x), r->d.rhs, c * n * 8, cudaMemcpyHostToDevice, st);
+        }
+        if (e != cudaSuccess) return fail_cuda(sl.h, e);
+    }
+    // tables: Newton job tables per law class, then the ragged solve arrays
+    size_t need = 0, nsys = 0;
+    for (Req *r : batch) {
+        need += up(r->table_bytes());
+        if (r->d.kind == TL_REQ_SOLVE) nsys += static_cast<size_t>(r->d.count);
+    }
+    tl_status ts = grow_stage(sl, need + 4 * Arena::kAlign);
+    if (ts != TL_OK) return ts;
+    size_t cur = 0;  // offset inside both the staging buffer and the scratch block
+    std::map<std::pair<int, int>, std::vector<Req *>> classes;
+    for (Req *r : batch)
+        if (r->d.kind == TL_REQ_NEWTON && r->d.count > 0) classes[{r->d.law.id, r->d.law.n}].push_back(r);
+    for (auto &kv : classes) {
+        const size_t tb = up(kv.second.size() * sizeof(NewtonJob));
+        NewtonJob *jobs = reinterpret_cast<NewtonJob *>(sl.stage + cur);
+        int64_t start = 0;
+        for (size_t j = 0; j < kv.second.size(); ++j) {
+            Req *r = kv.second[j];
+            NewtonJob jb = r->job;
+            jb.in = reinterpret_cast<const double *>(dptr(r->o_in));
+            jb.x = reinterpret_cast<double *>(dptr(r->o_x));
+            jb.out = r->has_aux() ? reinterpret_cast<double *>(dptr(r->o_aux)) : nullptr;
+            jb.iters = reinterpret_cast<int32_t *>(dptr(r->o_i1));
+            jb.status = reinterpret_cast<int32_t *>(dptr(r->o_i2));
+            jb.npoints = r->d.count;
+            jb.start = start;
+            start += r->d.count;
+            jobs[j] = jb;
+        }
+        char *dtab = dptr(sl.scratch_off + cur);
+        e = cudaMemcpyAsync(dtab, jobs, kv.second.size() * sizeof(NewtonJob), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return fail_cuda(sl.h, e);
+        NewtonBatch B{};
+        B.jobs = reinterpret_cast<const NewtonJob *>(dtab);
+        B.njobs = static_cast<int>(kv.second.size());
+        B.total = start;
+        B.rtol = cfg.rtol;
+        B.max_iter = cfg.max_iter;
+        ts = newton_launch(sl.h, kv.first.first, kv.first.second, B, st);
+        if (ts != TL_OK) return ts;
+        cur += tb;
+    }
+    if (nsys > 0) {
+        // n (int32), a_off, b_off, piv_off (int64), info (int32): element
+        // offsets relative to the arena base
+        int32_t *hn = reinterpret_cast<int32_t *>(sl.stage + cur);
+        int64_t *ha = reinterpret_cast<int64_t *>(sl.stage + cur + up(nsys * 4));
+        int64_t *hb = ha + nsys;
+        int64_t *hp = hb + nsys;
+        const size_t o_n = cur, o_a = cur + up(nsys * 4), o_info = o_a + up(nsys * 24);
+        size_t q = 0;
+        for (Req *r : batch) {
+            if (r->d.kind != TL_REQ_SOLVE) continue;
+            const int64_t n = r->d.n;
+            for (int64_t s = 0; s < r->d.count; ++s, ++q) {
+                hn[q] = static_cast<int32_t>(n);
+                ha[q] = static_cast<int64_t>(r->o_in / 8) + s * n * n;
+                hb[q] = static_cast<int64_t>(r->o_x / 8) + s * n;
+                hp[q] = static_cast<int64_t>(r->o_i1 / 4) + s * n;
+            }
+        }
+        e = cudaMemcpyAsync(dptr(sl.scratch_off + o_n), hn, o_info - o_n, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return fail_cuda(sl.h, e);
+        const int32_t *dn = reinterpret_cast<const int32_t *>(dptr(sl.scratch_off + o_n));
+        const int64_t *da = reinterpret_cast<const int64_t *>(dptr(sl.scratch_off + o_a));
+        int32_t *dinfo = reinterpret_cast<int32_t *>(dptr(sl.scratch_off + o_info));
+        const double *dbase = reinterpret_cast<const double *>(base);
+        ts = tl_lupp_solve_batched(sl.h, static_cast<int64_t>(nsys), dn, da, dbase, da + nsys, dbase,
+                                   reinterpret_cast<double *>(base), da + 2 * nsys, reinterpret_cast<int32_t *>(base),
+                                   dinfo, TL_PREC_FP64, nullptr, st);
+        if (ts != TL_OK) return ts;
+        // results of the solves (info from the tick table)
+        q = 0;
+        for (Req *r : batch) {
+            if (r->d.kind != TL_REQ_SOLVE) continue;
+            const size_t c = static_cast<size_t>(r->d.count);
+            e = cudaMemcpyAsync(r->d.i2, dinfo + q, c * 4, cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) return fail_cuda(sl.h, e);
+            q += c;
+        }
+    }
+    // outputs
+    for (Req *r : batch) {
+        const size_t c = static_cast<size_t>(r->d.count);
+        if (c == 0) continue;
+        if (r->d.kind == TL_REQ_NEWTON) {
+            e = cudaMemcpyAsync(r->d.x, dptr(r->o_x), c * r->xrows() * 8, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess && r->has_aux())
+                e = cudaMemcpyAsync(r->d.aux, dptr(r->o_aux), c * 6 * 8, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(r->d.i1, dptr(r->o_i1), c * 4, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(r->d.i2, dptr(r->o_i2), c * 4, cudaMemcpyDeviceToHost, st);
+        } else {
+            const size_t n = static_cast<size_t>(r->d.n);
+            e = cudaMemcpyAsync(r->d.x, dptr(r->o_x), c * n * 8, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(r->d.i1, dptr(r->o_i1), c * n * 4, cudaMemcpyDeviceToHost, st);
+        }
+        if (e != cudaSuccess) return fail_cuda(sl.h, e);
+    }
+    e = cudaEventRecord(sl.ev, st);
+    if (e != cudaSuccess) return fail_cuda(sl.h, e);
+    return TL_OK;
+}
+
+// Called with mu held: the slot's tick ended with `status`.
+void tl_server::finish(Slot &sl, int32_t status)
+{
+    const Clock::time_point now = Clock::now();
+    for (Req *r : sl.reqs) {
+        r->done = true;
+        r->status = status;
+        r->t_done = now;
+        if (r->off != SIZE_MAX) arena.release(r->off, r->bytes);
+        r->off = SIZE_MAX;
+        if (status == TL_OK) {
+            ++stats.completed;
+            stats.points += r->d.count;
+        } else {
+            ++stats.failed;
+        }
+    }
+    if (sl.scratch_off != SIZE_MAX) arena.release(sl.scratch_off, sl.scratch_bytes);
+    sl.scratch_off = SIZE_MAX;
+    sl.reqs.clear();
+    sl.busy = false;
+    cv_done.notify_all();
+}
+
+void tl_server::run()
+{
+    cudaSetDevice(device);
+    std::unique_lock<std::mutex> lk(mu);
+    for (;;) {
+        // retire finished ticks
+        bool any_busy = false;
+        for (Slot &sl : slots) {
+            if (!sl.busy) continue;
+            const cudaError_t q = cudaEventQuery(sl.ev);
+            if (q == cudaErrorNotReady) {
+                any_busy = true;
+                continue;
+            }
+            if (q != cudaSuccess) {
+                cudaGetLastError();
+                h->last_cuda_error = static_cast<int>(q);
+            }
+            finish(sl, q == cudaSuccess ? TL_OK : TL_ERR_CUDA);
+        }
+        if (stop && pending.empty() && !any_busy) break;
+        // admit the head of the queue into a free slot
+        Slot *free_slot = nullptr;
+        for (Slot &sl : slots)
+            if (!sl.busy) {
+                free_slot = &sl;
+                break;
+            }
+        bool launched = false;
+        if (free_slot && !pending.empty()) {
+            std::vector<Req *> batch;
+            size_t soff = SIZE_MAX, sbytes = 0;
+            if (form_tick(*free_slot, batch, soff, sbytes)) {
+                Slot &sl = *free_slot;
+                sl.busy = true;
+                sl.reqs = batch;
+                sl.scratch_off = soff;
+                sl.scratch_bytes = sbytes;
+                ++stats.ticks;
+                if (stats.arena_high_water < arena.high_water()) stats.arena_high_water = arena.high_water();
+                lk.unlock();
+                const tl_status ts = enqueue(sl, batch);
+                lk.lock();
+                if (ts != TL_OK) {
+                    // whatever was issued drains before the slot is reused
+                    cudaStreamSynchronize(sl.stream);
+                    cudaGetLastError();
+                    finish(sl, ts);
+                }
+                launched = true;
+            } else if (!any_busy) {
+                // nothing runs and the head still does not fit: it never will
+                Req *r = pending.front();
+                pending.pop_front();
+                r->done = true;
+                r->status = TL_ERR_NO_MEMORY;
+                r->t_done = Clock::now();
+                ++stats.failed;
+                cv_done.notify_all();
+                launched = true;
+            }
+        }
+        if (launched) continue;
+        if (any_busy) cv_work.wait_for(lk, std::chrono::microseconds(20));
+        else cv_work.wait(lk, [&] { return stop || !pending.empty(); });
+    }
+}
+
+extern "C" tl_status tl_server_create(tl_handle *h, const tl_server_config *cfg, tl_server **out)
+{
+    if (!h) return TL_ERR_INVALID_ARG;
+    if (!cfg || !out) return fail_arg(h, cfg ? 3 : 2);
+    if (cfg->budget_bytes < (1u << 20) || cfg->slots < 1 || cfg->slots > kMaxSlots || cfg->max_points_per_tick < 0 ||
+        !(cfg->rtol >= 0.0) || cfg->max_iter < 0)
+        return fail_arg(h, 2);
+    *out = nullptr;
+    tl_server *s = new tl_server();
+    s->h = h;
+    s->device = h->device;
+    s->cfg = *cfg;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&s->base), cfg->budget_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return TL_ERR_NO_MEMORY;
+    }
+    s->arena.reset(cfg->budget_bytes);
+    s->slots.resize(static_cast<size_t>(cfg->slots));
+    for (Slot &sl : s->slots) {
+        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess || tl_create(&sl.h) != TL_OK) {
+            cudaGetLastError();
+            tl_server_destroy(s);
+            return TL_ERR_CUDA;
+        }
+    }
+    s->loop = std::thread([s] { s->run(); });
+    *out = s;
+    return TL_OK;
+}
+
+extern "C" tl_status tl_server_submit(tl_server *s, const tl_request *req, int64_t *id)
+{
+    if (!s || !id) return TL_ERR_INVALID_ARG;
+    const tl_status st = check_request(req);
+    if (st != TL_OK) return st;
+    Req *r = new Req();
+    r->d = *req;
+    if (req->kind == TL_REQ_NEWTON) law_params(req->law, &r->job);
+    r->bytes = r->layout(0);
+    if (r->bytes + up(r->table_bytes()) + 4 * Arena::kAlign > s->arena.capacity()) {
+        delete r;
+        return TL_ERR_NO_MEMORY;
+    }
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) {
+            delete r;
+            return TL_ERR_INVALID_ARG;
+        }
+        r->id = s->next_id++;
+        s->reqs[r->id] = r;
+        ++s->stats.submitted;
+        s->pending.push_back(r);
+        *id = r->id;
+    }
+    s->cv_work.notify_one();
+    return TL_OK;
+}
+
+namespace {
+
+tl_status report(tl_server *s, std::unordered_map<int64_t, Req *>::iterator it, int32_t *req_status, double *latency_s)
+{
+    Req *r = it->second;
+    if (req_status) *req_status = r->status;
+    if (latency_s) *latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+    s->reqs.erase(it);
+    delete r;
+    return TL_OK;
+}
+
+}  // namespace
+
+extern "C" tl_status tl_server_test(tl_server *s, int64_t id, int32_t *done, int32_t *req_status, double *latency_s)
+{
+    if (!s || !done) return TL_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return TL_ERR_INVALID_ARG;
+    *done = it->second->done ? 1 : 0;
+    if (!*done) return TL_OK;
+    return report(s, it, req_status, latency_s);
+}
+
+extern "C" tl_status tl_server_wait(tl_server *s, int64_t id, double timeout_s, int32_t *req_status, double *latency_s)
+{
+    if (!s || !(timeout_s >= 0.0)) return TL_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return TL_ERR_INVALID_ARG;
+    Req *r = it->second;
+    const auto limit = Clock::now() + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(timeout_s));
+    if (!s->cv_done.wait_until(lk, limit, [&] { return r->done; })) return TL_ERR_TIMEOUT;
+    return report(s, s->reqs.find(id), req_status, latency_s);
+}
+
+extern "C" tl_status tl_server_stats_get(tl_server *s, tl_server_stats *out)
+{
+    if (!s || !out) return TL_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    *out = s->stats;
+    out->arena_high_water = s->arena.high_water();
+    return TL_OK;
+}
+
+extern "C" tl_status tl_server_destroy(tl_server *s)
+{
+    if (!s) return TL_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->loop.joinable()) s->loop.join();
+    for (Slot &sl : s->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+        if (sl.h) tl_destroy(sl.h);
+        if (sl.stage) cudaFreeHost(sl.stage);
+    }
+    cudaFree(s->base);
+    for (auto &kv : s->reqs) delete kv.second;
+    delete s;
+    return TL_OK;
+}

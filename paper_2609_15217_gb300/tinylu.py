@@ -35,6 +35,23 @@ _vp = C.c_void_p
 _i64 = C.c_int64
 _int = C.c_int
 
+TL_REQ_NEWTON, TL_REQ_SOLVE = 0, 1
+
+
+class tl_request(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n", C.c_int32), ("law", tl_law), ("count", C.c_int64),
+                ("ld_in", C.c_int64), ("in_", _vp), ("rhs", _vp), ("x", _vp), ("aux", _vp), ("i1", _vp), ("i2", _vp)]
+
+
+class tl_server_config(C.Structure):
+    _fields_ = [("budget_bytes", C.c_size_t), ("slots", C.c_int32), ("max_points_per_tick", C.c_int64),
+                ("rtol", C.c_double), ("max_iter", C.c_int32)]
+
+
+class tl_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("ticks", C.c_int64),
+                ("points", C.c_int64), ("arena_high_water", C.c_size_t)]
+
 _SIGS = {
     "tl_create": ([C.POINTER(_vp)], _int),
     "tl_destroy": ([_vp], _int),
@@ -47,9 +64,17 @@ _SIGS = {
     "tl_lupp_solve_batched": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _int, _vp, _vp], _int),
     "tl_lupp_solve_batched_noalloc": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _int),
     "tl_newton_integrate": ([_vp, C.POINTER(tl_law), _i64, _vp, _vp, _vp, _vp, _vp, C.c_double, _int, _vp], _int),
+    "tl_newton_integrate_tangent": ([_vp, C.POINTER(tl_law), _i64, _vp, _vp, _vp, _vp, _vp, _vp, C.c_double,
+                                     _int, _vp], _int),
     "tl_newton_integrate_cpu_driven": ([_vp, C.POINTER(tl_law), _i64, _vp, _vp, _vp, _vp, _vp, C.c_double, _int,
                                         _vp], _int),
     "tl_autotune": ([_vp, _int, _int, _int, C.c_char_p], _int),
+    "tl_server_create": ([_vp, C.POINTER(tl_server_config), C.POINTER(_vp)], _int),
+    "tl_server_submit": ([_vp, C.POINTER(tl_request), C.POINTER(_i64)], _int),
+    "tl_server_test": ([_vp, _i64, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_double)], _int),
+    "tl_server_wait": ([_vp, _i64, C.c_double, C.POINTER(C.c_int32), C.POINTER(C.c_double)], _int),
+    "tl_server_stats_get": ([_vp, C.POINTER(tl_server_stats)], _int),
+    "tl_server_destroy": ([_vp], _int),
     "tl_dispatch_set": ([_vp, _int, _int, _int, _int], _int),
     "tl_dispatch_get": ([_vp, _int, _int, C.POINTER(_int), C.POINTER(_int)], _int),
 }
@@ -171,6 +196,12 @@ def tl_newton_integrate(h, law, npoints, inputs, x, outputs, iterations, status,
                                     _p(status), rtol, max_iter, _stream(stream))
 
 
+def tl_newton_integrate_tangent(h, law, npoints, inputs, x, outputs, tangent, iterations, status, rtol, max_iter,
+                                stream=None):
+    return _lib.tl_newton_integrate_tangent(h, C.byref(law), npoints, _p(inputs), _p(x), _p(outputs), _p(tangent),
+                                            _p(iterations), _p(status), rtol, max_iter, _stream(stream))
+
+
 def tl_newton_integrate_cpu_driven(h, law, npoints, inputs, x, outputs, iterations, status, rtol, max_iter,
                                    stream=None):
     return _lib.tl_newton_integrate_cpu_driven(h, C.byref(law), npoints, _p(inputs), _p(x), _p(outputs),
@@ -190,6 +221,58 @@ def tl_dispatch_get(h, n, layout):
     v, b = C.c_int(0), C.c_int(0)
     st = _lib.tl_dispatch_get(h, n, layout, C.byref(v), C.byref(b))
     return st, v.value, b.value
+
+
+def make_request(kind, count, in_, x, i1, i2, law=None, n=0, rhs=None, aux=None, ld_in=0):
+    """A tl_request over host arrays (numpy arrays or raw addresses)."""
+    r = tl_request()
+    r.kind = kind
+    r.n = n
+    if law is not None:
+        r.law = law
+    r.count = count
+    r.ld_in = ld_in
+    r.in_, r.rhs, r.x, r.aux, r.i1, r.i2 = (_p(v) for v in (in_, rhs, x, aux, i1, i2))
+    return r
+
+
+def tl_server_create(h, budget_bytes, slots=4, max_points_per_tick=1 << 20, rtol=1e-10, max_iter=20):
+    """Returns (status, server handle)."""
+    cfg = tl_server_config(budget_bytes, slots, max_points_per_tick, rtol, max_iter)
+    out = _vp()
+    st = _lib.tl_server_create(h, C.byref(cfg), C.byref(out))
+    return st, out.value
+
+
+def tl_server_submit(s, req):
+    """Returns (status, request id)."""
+    rid = _i64(0)
+    st = _lib.tl_server_submit(s, C.byref(req), C.byref(rid))
+    return st, rid.value
+
+
+def tl_server_test(s, rid):
+    """Returns (status, done, request status, latency in s)."""
+    done, rs, lat = C.c_int32(0), C.c_int32(0), C.c_double(0.0)
+    st = _lib.tl_server_test(s, rid, C.byref(done), C.byref(rs), C.byref(lat))
+    return st, done.value, rs.value, lat.value
+
+
+def tl_server_wait(s, rid, timeout_s=60.0):
+    """Returns (status, request status, latency in s)."""
+    rs, lat = C.c_int32(0), C.c_double(0.0)
+    st = _lib.tl_server_wait(s, rid, timeout_s, C.byref(rs), C.byref(lat))
+    return st, rs.value, lat.value
+
+
+def tl_server_stats_get(s):
+    out = tl_server_stats()
+    st = _lib.tl_server_stats_get(s, C.byref(out))
+    return st, {k: getattr(out, k) for k, _ in tl_server_stats._fields_}
+
+
+def tl_server_destroy(s):
+    return _lib.tl_server_destroy(s)
 
 
 def variant_id(lanes, shared=False):

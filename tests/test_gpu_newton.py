@@ -129,3 +129,41 @@ def test_newton_argument_errors(tl, h):
     assert tl.tl_newton_integrate(h, law, 0, d, d, None, i, i, 1e-10, 20) == tl.TL_OK
     law = tl.make_law(99, 7)
     assert tl.tl_newton_integrate(h, law, 4, d, d, None, i, i, 1e-10, 20) == tl.TL_ERR_INVALID_ARG
+
+
+def test_norton_tangent_parity(tl, h):
+    """Consistent tangent (Sec. 4.3, multi-RHS solve after convergence)
+    against the oracle's, point by point; states and counts unchanged."""
+    npts = 4000 + 17
+    prm = oracle.norton_params()
+    sig0, deps = inputs.norton_points(npts, 4242)
+    sig0[5] = np.nan                     # a non-finite point: NaN tangent
+    r = oracle.newton_norton(prm, sig0, deps, rtol=1e-10, max_iter=20)
+    fields = np.ascontiguousarray(np.concatenate([sig0.T, deps.T], axis=0))
+    d_in = torch.from_numpy(fields).to(DEV)
+    d_x = torch.empty((7, npts), dtype=torch.float64, device=DEV)
+    d_sig = torch.empty((6, npts), dtype=torch.float64, device=DEV)
+    d_D = torch.full((36, npts), -7.0, dtype=torch.float64, device=DEV)
+    d_it = torch.empty(npts, dtype=torch.int32, device=DEV)
+    d_st = torch.empty(npts, dtype=torch.int32, device=DEV)
+    law = tl.make_law(tl.TL_LAW_NORTON, 7, prm)
+    tl.check("tangent", tl.tl_newton_integrate_tangent(h, law, npts, d_in, d_x, d_sig, d_D, d_it, d_st, 1e-10, 20), h)
+    torch.cuda.synchronize()
+    x_g, it_g, st_g = d_x.cpu().numpy().T, d_it.cpu().numpy(), d_st.cpu().numpy()
+    D_g = d_D.cpu().numpy().T.reshape(npts, 6, 6).transpose(0, 2, 1)   # [p, i, j]
+    x_f, it_f, st_f, _ = gpu_norton(tl, h, prm, sig0, deps)
+    assert np.array_equal(x_g.view(np.int64), x_f.view(np.int64)) and np.array_equal(it_g, it_f)
+    assert st_g[5] == 3 and np.isnan(D_g[5]).all()
+    ok = (r["status"] == 0) & (st_g == 0)
+    assert ok.sum() == npts - 1
+    worst = 0.0
+    for p in np.nonzero(ok)[0][::7]:
+        D_o, info = oracle.norton_tangent(prm, sig0[p], deps[p], x_g[p])
+        assert info == 0
+        worst = max(worst, np.abs(D_g[p] - D_o).max() / np.abs(D_o).max())
+    assert worst <= 1e-12, worst
+    law7 = tl.make_law(tl.TL_LAW_TANH, 7)
+    assert tl.tl_newton_integrate_tangent(h, law7, 4, d_in, d_x, None, d_D, d_it, d_st, 1e-10, 20) == \
+        tl.TL_ERR_UNSUPPORTED
+    assert tl.tl_newton_integrate_tangent(h, law, 4, d_in, d_x, None, None, d_it, d_st, 1e-10, 20) == \
+        tl.TL_ERR_INVALID_ARG
