@@ -21,6 +21,8 @@ Linear Systems on GPUs: Application to Constitutive Laws"):
   * tanh_eval -- synthetic law F(x) = A x + c*tanh(x) - b.
   * norton_tangent -- consistent tangent operator at a converged state
     (Sec. 4.3, the multi-right-hand-side solve after convergence).
+  * getrf_tiled -- tile-local pivoting of the paper's Tiled solvers
+    (Sec. 3.2), with the acceptance threshold of Sec. 4.1.
   * sgetrf / ir_gesv -- binary32 factorization and binary64 iterative
     refinement (not in the paper: the published scheme of Langou et al.
     2006, as LAPACK's dsgesv, with every operation's format and order
@@ -61,6 +63,8 @@ def _declare(lib):
     lib.orc_getrf_batch.argtypes = [C.c_int, C.c_int64, _d, _i32, _i32, _d, C.c_int]
     lib.orc_getrs_batch.restype = None
     lib.orc_getrs_batch.argtypes = [C.c_int, C.c_int64, _d, _i32, _d, C.c_int]
+    lib.orc_getrf_tiled_batch.restype = None
+    lib.orc_getrf_tiled_batch.argtypes = [C.c_int, C.c_int64, _d, _i32, _i32, _i32, C.c_int, C.c_double, C.c_int]
     lib.orc_sgetrf.restype = C.c_int
     lib.orc_sgetrf.argtypes = [C.c_int, C.POINTER(C.c_float), _i32]
     lib.orc_ir_gesv_batch.restype = None
@@ -121,6 +125,23 @@ def getrf(A, nthreads=0, lib=None):
     gap = np.zeros(batch, np.float64)
     lib.orc_getrf_batch(n, batch, _ptr(Acm), _ptr(ipiv, _i32), _ptr(info, _i32), _ptr(gap), nthreads)
     return _mathidx(Acm), ipiv, info, gap
+
+
+def getrf_tiled(A, tile, threshold=1e-10, nthreads=0, lib=None):
+    """LU with tile-local pivoting (Sec. 3.2, Tiled solvers): the pivot is
+    sought in the diagonal tile of `tile` rows and below it only when the
+    in-tile best is under `threshold`.  Returns (LU, ipiv, info,
+    out_of_tile) where out_of_tile counts the steps that looked below the
+    tile."""
+    lib = lib or load()
+    Acm = _colmajor(A)
+    batch, n = Acm.shape[0], Acm.shape[1]
+    ipiv = np.zeros((batch, n), np.int32)
+    info = np.zeros(batch, np.int32)
+    oot = np.zeros(batch, np.int32)
+    lib.orc_getrf_tiled_batch(n, batch, _ptr(Acm), _ptr(ipiv, _i32), _ptr(info, _i32), _ptr(oot, _i32), tile,
+                              threshold, nthreads)
+    return _mathidx(Acm), ipiv, info, oot
 
 
 def getrs(LU, ipiv, B, nthreads=0, lib=None):

@@ -20,6 +20,8 @@
  *   orc_getrf   -- Gaussian elimination with partial pivoting, PA = LU,
  *                  right-looking, one column per step (Sec. 2.2).
  *   orc_getrs   -- Ly = Pb then Ux = y (Sec. 2.2).
+ *   orc_getrf_tiled -- the same elimination with tile-local pivoting
+ *                  (Sec. 3.2, Tiled solvers; acceptance threshold).
  *   orc_gesv    -- getrf + getrs, fused (Sec. 3.1, MAGMA gesv).
  *   orc_newton_* -- Newton-Raphson, Eqs. (1)-(3) of Sec. 2.1, driven per
  *                  point as in Algorithm 2.
@@ -87,10 +89,12 @@ static int mag_greater(double a, double b)
  *
  * Returns info.
  */
-int orc_getrf(int n, double *a, int32_t *ipiv, double *min_gap)
+static int getrf_core(int n, double *a, int32_t *ipiv, double *min_gap, int tile, double threshold,
+                      int *out_of_tile)
 {
-    int info = 0;
+    int info = 0, outside = 0;
     double gap = INFINITY;
+    if (out_of_tile) *out_of_tile = 0;
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i)
             if (!isfinite(AT(a, n, i, j))) {
@@ -100,9 +104,21 @@ int orc_getrf(int n, double *a, int32_t *ipiv, double *min_gap)
             }
 
     for (int k = 0; k < n; ++k) {
+        /* candidate rows: k .. hi-1 (the diagonal tile), all rows below k
+         * when the tile's best is under the threshold */
+        int hi = n;
+        if (tile > 0 && tile < n) {
+            hi = (k / tile + 1) * tile;
+            if (hi > n) hi = n;
+        }
         int p = k;
-        for (int i = k + 1; i < n; ++i)
+        for (int i = k + 1; i < hi; ++i)
             if (mag_greater(AT(a, n, i, k), AT(a, n, p, k))) p = i;
+        if (hi < n && fabs(AT(a, n, p, k)) < threshold) {
+            ++outside;
+            for (int i = hi; i < n; ++i)
+                if (mag_greater(AT(a, n, i, k), AT(a, n, p, k))) p = i;
+        }
         ipiv[k] = p + 1;
 
         if (k + 1 < n && AT(a, n, p, k) != 0.0) {
@@ -135,7 +151,49 @@ int orc_getrf(int n, double *a, int32_t *ipiv, double *min_gap)
                 AT(a, n, i, j) = fma(-AT(a, n, i, k), AT(a, n, k, j), AT(a, n, i, j));
     }
     if (min_gap) *min_gap = gap;
+    if (out_of_tile) *out_of_tile = outside;
     return info;
+}
+
+int orc_getrf(int n, double *a, int32_t *ipiv, double *min_gap)
+{
+    return getrf_core(n, a, ipiv, min_gap, 0, 0.0, NULL);
+}
+
+/*
+ * orc_getrf_tiled: LU with tile-local pivoting (Sec. 3.2, the Tiled solvers:
+ * the pivot row is sought inside the diagonal tile, and rows below it are
+ * considered only when the best in-tile candidate falls below an acceptance
+ * threshold).  Reading taken: the matrix is cut into tiles of `tile` rows;
+ * at step k the candidates are the rows k .. min(n, (k/tile + 1) tile) - 1
+ * of the diagonal tile, first maximum as orc_getrf; if that maximum is
+ * below `threshold` in magnitude (absolute), the candidates are all rows
+ * k .. n-1 instead (first maximum over them).  Everything else is
+ * orc_getrf: zero pivots, row swaps, multipliers, updates, non-finite input.
+ * tile <= 0 or tile >= n is textbook partial pivoting (orc_getrf is
+ * getrf_core with no tile).  *out_of_tile (nullable) counts the steps that
+ * looked below the tile.  Returns info.
+ */
+int orc_getrf_tiled(int n, double *a, int32_t *ipiv, int tile, double threshold, int *out_of_tile)
+{
+    return getrf_core(n, a, ipiv, NULL, tile, threshold, out_of_tile);
+}
+
+/* Batched tile-local factor (one system per s, as orc_getrf_batch). */
+void orc_getrf_tiled_batch(int n, int64_t batch, double *A, int32_t *ipiv, int32_t *info, int32_t *out_of_tile,
+                           int tile, double threshold, int nthreads)
+{
+    const size_t nn = (size_t)n * (size_t)n;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+#endif
+    for (int64_t s = 0; s < batch; ++s) {
+        int o = 0;
+        info[s] = orc_getrf_tiled(n, A + (size_t)s * nn, ipiv + (size_t)s * n, tile, threshold, &o);
+        out_of_tile[s] = o;
+    }
+    (void)nthreads;
 }
 
 /*

@@ -311,3 +311,41 @@ def test_threads_do_not_change_results():
     r2 = oracle.gesv(A, b, nthreads=0)
     for u, v in zip(r1, r2):
         assert np.array_equal(u, v, equal_nan=True)
+
+
+# ---------------------------------------------------------------------------
+# Tile-local pivoting (Sec. 3.2, Tiled solvers; 1e-10 threshold of Sec. 4.1)
+# ---------------------------------------------------------------------------
+
+def pin_tiled(lib=None):
+    for n in (5, 12, 32):
+        A, b = inputs.uniform_systems(n, 40, 6000 + n, -0.5, 0.5)
+        LU, piv, info, _ = oracle.getrf(A, lib=lib)
+        # one tile covering the matrix, or an infinite threshold: textbook
+        for tile, thr in ((n, 1e-10), (0, 1e-10), (2, np.inf)):
+            LUt, pivt, infot, oot = oracle.getrf_tiled(A, tile, thr, lib=lib)
+            assert np.array_equal(pivt, piv) and np.array_equal(LUt.view(np.int64), LU.view(np.int64))
+        # the default distribution never looks below a tile (Sec. 4.1)
+        for tile in (2, 3, 6):
+            LUt, pivt, infot, oot = oracle.getrf_tiled(A, tile, 1e-10, lib=lib)
+            assert (oot == 0).all() and (infot == 0).all()
+            # every pivot stays inside its diagonal tile
+            k = np.arange(n)
+            hi = np.minimum((k // tile + 1) * tile, n)
+            assert ((pivt - 1 >= k) & (pivt - 1 < hi)).all()
+            # PA = LU with the permutation of the tile-local pivots
+            for s in range(5):
+                P = _perm_from_ipiv(pivt[s])
+                L, U = _split_lu(LUt[s])
+                assert np.abs(A[s][P] - L @ U).max() <= 4 * n * EPS * (np.abs(L) @ np.abs(U)).max()
+        # the stress distribution U[+-5e-10] triggers lower-tile searches,
+        # and a 2^31 scaling (entries above the threshold) suppresses them
+        S = A * 1e-9
+        _, pivs, _, oot = oracle.getrf_tiled(S, 2, 1e-10, lib=lib)
+        assert (oot > 0).mean() > 0.3
+        _, pivb, _, ootb = oracle.getrf_tiled(np.ldexp(S, 40), 2, 1e-10, lib=lib)
+        assert (ootb == 0).all()
+
+
+def test_tiled_pivoting_pins():
+    pin_tiled()

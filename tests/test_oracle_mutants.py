@@ -21,6 +21,7 @@ from oracle import build as obuild
 from paper_2609_15217_gb300 import inputs
 
 from test_oracle_ir import IR_PINS
+from test_oracle_lupp import pin_tiled
 from test_oracle_newton import pin_tangent, radial_return
 
 EPS = np.finfo(np.float64).eps
@@ -55,6 +56,8 @@ MUTATIONS = {
     "newton_absolute_test": ("if (r <= rtol * r0 || r0 == 0.0)", "if (r <= rtol || r0 == 0.0)"),
     "newton_counts_evals": ("        ++k;\n        eval(ctx, x, F, J);", "        k += 2;\n        eval(ctx, x, F, J);"),
     "tanh_jacobian_sign": ("c[i] * (1.0 - t * t)", "c[i] * (1.0 + t * t)"),
+    "tiled_never_looks_below": ("if (hi < n && fabs(AT(a, n, p, k)) < threshold) {", "if (0) {"),
+    "tiled_tile_too_tall": ("hi = (k / tile + 1) * tile;", "hi = (k / tile + 2) * tile;"),
     "tangent_rhs_sign": ("for (int i = 0; i < 7; ++i) X[i] = (i == j) ? 1.0 : 0.0;",
                          "for (int i = 0; i < 7; ++i) X[i] = (i == j) ? -1.0 : 0.0;"),
     "tangent_drops_lambda": ("D[i + 6 * j] = 2.0 * mu * X[i] + (i < 3 ? lambda * tr : 0.0);",
@@ -171,7 +174,7 @@ def pin_tanh(lib):
         assert np.array_equal(r1["x"], r2["x"])
 
 
-PINS = [pin_golden, pin_reconstruction_and_errors, pin_singular, pin_norton, pin_tanh, pin_tangent, *IR_PINS]
+PINS = [pin_golden, pin_reconstruction_and_errors, pin_singular, pin_norton, pin_tanh, pin_tangent, pin_tiled, *IR_PINS]
 
 
 def failing_pins(lib):
