@@ -667,6 +667,9 @@ def main():
     ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--dispatch-table", default=None,
+                    help="interleaved-layout dispatch table (JSON written by tl_autotune) to apply instead of "
+                         "autotuning, e.g. to profile the same kernels the timed run used")
     ap.add_argument("--batch", type=int, default=None,
                     help="cap on systems per n (small cases for profiling; the default is the full sweep)")
     ap.add_argument("--ref-seconds-per-n", type=float, default=0.3)
@@ -697,7 +700,13 @@ def main():
     h = tl.tl_create()
     n_list = list(range(args.nmin, args.nmax + 1))
     tune = {}
-    if not args.no_autotune:
+    if args.dispatch_table:
+        with open(args.dispatch_table) as f:
+            entries = json.load(f)["entries"]
+        for e in entries:
+            tl.check("tl_dispatch_set", tl.tl_dispatch_set(h, e["n"], 1, e["variant"], e["block"]), h)
+        tune[1] = {e["n"]: e["variant"] for e in entries}
+    elif not args.no_autotune:
         # size-aware dispatcher: time every kernel variant per n once, before
         # anything is timed (the "best X" selection of the paper's Sec. 4.1)
         log("autotune")

@@ -160,6 +160,22 @@ tl_status tl_gesv_batched(tl_handle *h, int n, const double *A, double *LU_out, 
                           int64_t ld_batch, int64_t batch, cudaStream_t stream);
 
 /*
+ * tl_gesv_batched_tilepiv -- tl_gesv_batched with the tile-local pivoting of
+ * the paper's Tiled solvers (Sec. 3.2; threshold 1e-10 in Sec. 4.1): the
+ * pivot of step k is the first maximum over the rows of the diagonal tile
+ * (rows k .. min(n, (k/tile + 1) tile) - 1), and over all rows k .. n-1
+ * only when that maximum is below `threshold` in magnitude.  This is not
+ * textbook partial pivoting: pivots, factors and x differ from
+ * tl_gesv_batched whenever a step keeps an in-tile pivot that a full-column
+ * search would not take (the stability cost the paper quantifies); tile 0
+ * or tile >= n is textbook partial pivoting.  Arguments after threshold as
+ * tl_gesv_batched (numbered 5..14).  Runs the shared-memory kernels.
+ */
+tl_status tl_gesv_batched_tilepiv(tl_handle *h, int n, int tile, double threshold, const double *A,
+                                  double *LU_out, const double *b, double *x, int32_t *ipiv, int32_t *info,
+                                  tl_layout layout, int64_t ld_batch, int64_t batch, cudaStream_t stream);
+
+/*
  * tl_lupp_solve_batched -- ragged batch: system s has its own size n[s]
  * (1..32) and lives anywhere in the A / b / ipiv arrays (per-system
  * column-major storage at the given element offsets).

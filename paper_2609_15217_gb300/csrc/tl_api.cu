@@ -7,6 +7,7 @@
 #include <climits>
 #include <cstdio>
 #include <cstring>
+#include <cmath>
 #include <new>
 #include <unordered_map>
 
@@ -298,6 +299,37 @@ tl_status tl_gesv_batched(tl_handle *h, int n, const double *A, double *LU_out, 
     if (!info || misaligned(info, 4)) return fail_arg(h, 8);
     SolveArgs a{A, LU_out, b, x, ipiv, info, ld_batch, batch, 1};
     return launch_op(h, n, layout, LU_out ? kOpGesvLU : kOpGesv, a, stream);
+}
+
+tl_status tl_gesv_batched_tilepiv(tl_handle *h, int n, int tile, double threshold, const double *A,
+                                  double *LU_out, const double *b, double *x, int32_t *ipiv, int32_t *info,
+                                  tl_layout layout, int64_t ld_batch, int64_t batch, cudaStream_t stream)
+{
+    if (!h) return TL_ERR_INVALID_ARG;
+    h->last_bad_arg = 0;
+    if (n < 1 || n > TL_MAX_N) return fail_arg(h, 2);
+    if (tile < 0) return fail_arg(h, 3);
+    if (!(threshold >= 0.0) || !std::isfinite(threshold)) return fail_arg(h, 4);
+    if (layout != TL_LAYOUT_PER_SYSTEM && layout != TL_LAYOUT_INTERLEAVED) return fail_arg(h, 11);
+    if (batch < 0) return fail_arg(h, 13);
+    if (layout == TL_LAYOUT_INTERLEAVED && ld_batch < batch) return fail_arg(h, 12);
+    if (batch == 0) return TL_OK;
+    if (!A || misaligned(A, 8)) return fail_arg(h, 5);
+    if (LU_out && misaligned(LU_out, 8)) return fail_arg(h, 6);
+    if (!b || misaligned(b, 8)) return fail_arg(h, 7);
+    if (!x || misaligned(x, 8)) return fail_arg(h, 8);
+    if (!ipiv || misaligned(ipiv, 4)) return fail_arg(h, 9);
+    if (!info || misaligned(info, 4)) return fail_arg(h, 10);
+    SolveArgs a{A, LU_out, b, x, ipiv, info, ld_batch, batch, 1};
+    a.tile = (tile >= n) ? 0 : tile;
+    a.threshold = threshold;
+    const int op = LU_out ? kOpGesvLU : kOpGesv;
+    if (n == 1) return launch_op(h, n, layout, op, a, stream);  // nothing to pivot
+    // the shared-memory kernels (run-time n) carry the tile-local search
+    const int lanes = n <= 6 ? 2 : n <= 12 ? 4 : n <= 20 ? 8 : 16;
+    const Variant *v = find_variant(n, layout, op, variant_id(lanes, 1));
+    if (!v || v->kind != 1) return TL_ERR_UNSUPPORTED;
+    return launch_variant(h, v, n, 0, a, stream);
 }
 
 }  // extern "C"

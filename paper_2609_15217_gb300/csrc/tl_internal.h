@@ -23,6 +23,9 @@ struct SolveArgs {
     int64_t ld;
     int64_t batch;
     int nrhs;
+    // tile-local pivoting (shared-memory kernels only): 0 = textbook
+    int tile;
+    double threshold;
 };
 
 // Arguments of the ragged-batch kernels (tl_lupp_solve_batched): the

@@ -8,7 +8,8 @@
 // Newton kernel of its law class (one launch per class over every request of
 // the tick, through a job table) or its systems solved by one ragged LUpp
 // over every solve of the tick -> results copied back to its host arrays ->
-// done when the tick's event completes (its arena block is released then).
+// done when its group's event completes (its arena block is released then;
+// the tick's tables when the last group of the tick completes).
 // Ticks on different slots overlap on the device; requests that arrive while
 // ticks run wait at most until a slot frees up.
 //
@@ -78,12 +79,22 @@ struct Req {
     }
 };
 
+// Requests of a tick that complete together: one Newton law class, all the
+// solves, or the empty requests; `ev` (slot.evs[index]) is recorded after
+// the group's results are copied back.
+struct Group {
+    std::vector<Req *> reqs;
+    bool done = false;
+};
+constexpr int kMaxGroups = 2 * TL_MAX_N + 8;
+
 struct Slot {
     cudaStream_t stream = nullptr;
-    cudaEvent_t ev = nullptr;
+    std::vector<cudaEvent_t> evs;  // kMaxGroups events
     tl_handle *h = nullptr;  // own handle: the ragged solve's workspace is per handle
     bool busy = false;
     std::vector<Req *> reqs;
+    std::vector<Group> groups;
     size_t scratch_off = SIZE_MAX, scratch_bytes = 0;
     char *stage = nullptr;  // page-locked staging of the tick tables
     size_t stage_bytes = 0;
@@ -113,7 +124,8 @@ struct tl_server {
     void run();
     bool form_tick(Slot &sl, std::vector<Req *> &batch, size_t &scratch_off, size_t &scratch_bytes);
     tl_status enqueue(Slot &sl, std::vector<Req *> &batch);
-    void finish(Slot &sl, int32_t status);
+    void finish_group(Slot &sl, Group &g, int32_t status);
+    void retire(Slot &sl, tl_status failed);
 };
 
 namespace {
@@ -189,42 +201,72 @@ bool tl_server::form_tick(Slot &, std::vector<Req *> &batch, size_t &scratch_off
 }
 
 // Issue a tick's copies and kernels on the slot's stream (no lock held).
+// Each group copies its inputs in, runs, copies its results out and records
+// its event, cheapest law class first, so a request waits only for its own
+// group and the groups issued before it.
 tl_status tl_server::enqueue(Slot &sl, std::vector<Req *> &batch)
 {
     cudaStream_t st = sl.stream;
     cudaError_t e = cudaSuccess;
     auto dptr = [&](size_t off) { return base + off; };
-    // inputs
-    for (Req *r : batch) {
-        const size_t c = static_cast<size_t>(r->d.count);
-        if (c == 0) continue;
-        if (r->d.kind == TL_REQ_NEWTON) {
-            const size_t ld = r->d.ld_in > 0 ? static_cast<size_t>(r->d.ld_in) : c;
-            if (ld == c)
-                e = cudaMemcpyAsync(dptr(r->o_in), r->d.in, c * r->fields() * 8, cudaMemcpyHostToDevice, st);
-            else
-                e = cudaMemcpy2DAsync(dptr(r->o_in), c * 8, r->d.in, ld * 8, c * 8, static_cast<size_t>(r->fields()),
-                                      cudaMemcpyHostToDevice, st);
-        } else {
-            const size_t n = static_cast<size_t>(r->d.n);
-            e = cudaMemcpyAsync(dptr(r->o_in), r->d.in, c * n * n * 8, cudaMemcpyHostToDevice, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(dptr(r->o_x), r->d.rhs, c * n * 8, cudaMemcpyHostToDevice, st);
-        }
-        if (e != cudaSuccess) return fail_cuda(sl.h, e);
-    }
-    // tables: Newton job tables per law class, then the ragged solve arrays
+    sl.groups.clear();
+    std::map<std::pair<int, int>, std::vector<Req *>> classes;  // (law, n): Norton first, then tanh by n
+    std::vector<Req *> solves, empties;
     size_t need = 0, nsys = 0;
     for (Req *r : batch) {
         need += up(r->table_bytes());
-        if (r->d.kind == TL_REQ_SOLVE) nsys += static_cast<size_t>(r->d.count);
+        if (r->d.count == 0) empties.push_back(r);
+        else if (r->d.kind == TL_REQ_NEWTON) classes[{r->d.law.id, r->d.law.n}].push_back(r);
+        else {
+            solves.push_back(r);
+            nsys += static_cast<size_t>(r->d.count);
+        }
     }
     tl_status ts = grow_stage(sl, need + 4 * Arena::kAlign);
     if (ts != TL_OK) return ts;
+    auto close_group = [&](std::vector<Req *> &reqs) -> tl_status {
+        const size_t g = sl.groups.size();
+        if (g >= sl.evs.size()) return TL_ERR_UNSUPPORTED;
+        const cudaError_t er = cudaEventRecord(sl.evs[g], st);
+        if (er != cudaSuccess) return fail_cuda(sl.h, er);
+        sl.groups.push_back(Group{reqs, false});
+        return TL_OK;
+    };
+    auto copy_in = [&](Req *r) -> cudaError_t {
+        const size_t c = static_cast<size_t>(r->d.count);
+        if (r->d.kind == TL_REQ_NEWTON) {
+            const size_t ld = r->d.ld_in > 0 ? static_cast<size_t>(r->d.ld_in) : c;
+            if (ld == c) return cudaMemcpyAsync(dptr(r->o_in), r->d.in, c * r->fields() * 8, cudaMemcpyHostToDevice, st);
+            return cudaMemcpy2DAsync(dptr(r->o_in), c * 8, r->d.in, ld * 8, c * 8, static_cast<size_t>(r->fields()),
+                                     cudaMemcpyHostToDevice, st);
+        }
+        const size_t n = static_cast<size_t>(r->d.n);
+        cudaError_t er = cudaMemcpyAsync(dptr(r->o_in), r->d.in, c * n * n * 8, cudaMemcpyHostToDevice, st);
+        if (er == cudaSuccess) er = cudaMemcpyAsync(dptr(r->o_x), r->d.rhs, c * n * 8, cudaMemcpyHostToDevice, st);
+        return er;
+    };
+    auto copy_out = [&](Req *r) -> cudaError_t {
+        const size_t c = static_cast<size_t>(r->d.count);
+        cudaError_t er;
+        if (r->d.kind == TL_REQ_NEWTON) {
+            er = cudaMemcpyAsync(r->d.x, dptr(r->o_x), c * r->xrows() * 8, cudaMemcpyDeviceToHost, st);
+            if (er == cudaSuccess && r->has_aux())
+                er = cudaMemcpyAsync(r->d.aux, dptr(r->o_aux), c * 6 * 8, cudaMemcpyDeviceToHost, st);
+            if (er == cudaSuccess) er = cudaMemcpyAsync(r->d.i1, dptr(r->o_i1), c * 4, cudaMemcpyDeviceToHost, st);
+            if (er == cudaSuccess) er = cudaMemcpyAsync(r->d.i2, dptr(r->o_i2), c * 4, cudaMemcpyDeviceToHost, st);
+        } else {
+            const size_t n = static_cast<size_t>(r->d.n);
+            er = cudaMemcpyAsync(r->d.x, dptr(r->o_x), c * n * 8, cudaMemcpyDeviceToHost, st);
+            if (er == cudaSuccess) er = cudaMemcpyAsync(r->d.i1, dptr(r->o_i1), c * n * 4, cudaMemcpyDeviceToHost, st);
+        }
+        return er;
+    };
+
+    if (!empties.empty() && (ts = close_group(empties)) != TL_OK) return ts;
     size_t cur = 0;  // offset inside both the staging buffer and the scratch block
-    std::map<std::pair<int, int>, std::vector<Req *>> classes;
-    for (Req *r : batch)
-        if (r->d.kind == TL_REQ_NEWTON && r->d.count > 0) classes[{r->d.law.id, r->d.law.n}].push_back(r);
     for (auto &kv : classes) {
+        for (Req *r : kv.second)
+            if ((e = copy_in(r)) != cudaSuccess) return fail_cuda(sl.h, e);
         const size_t tb = up(kv.second.size() * sizeof(NewtonJob));
         NewtonJob *jobs = reinterpret_cast<NewtonJob *>(sl.stage + cur);
         int64_t start = 0;
@@ -234,6 +276,7 @@ tl_status tl_server::enqueue(Slot &sl, std::vector<Req *> &batch)
             jb.in = reinterpret_cast<const double *>(dptr(r->o_in));
             jb.x = reinterpret_cast<double *>(dptr(r->o_x));
             jb.out = r->has_aux() ? reinterpret_cast<double *>(dptr(r->o_aux)) : nullptr;
+            jb.tangent = nullptr;
             jb.iters = reinterpret_cast<int32_t *>(dptr(r->o_i1));
             jb.status = reinterpret_cast<int32_t *>(dptr(r->o_i2));
             jb.npoints = r->d.count;
@@ -253,8 +296,13 @@ tl_status tl_server::enqueue(Slot &sl, std::vector<Req *> &batch)
         ts = newton_launch(sl.h, kv.first.first, kv.first.second, B, st);
         if (ts != TL_OK) return ts;
         cur += tb;
+        for (Req *r : kv.second)
+            if ((e = copy_out(r)) != cudaSuccess) return fail_cuda(sl.h, e);
+        if ((ts = close_group(kv.second)) != TL_OK) return ts;
     }
     if (nsys > 0) {
+        for (Req *r : solves)
+            if ((e = copy_in(r)) != cudaSuccess) return fail_cuda(sl.h, e);
         // n (int32), a_off, b_off, piv_off (int64), info (int32): element
         // offsets relative to the arena base
         int32_t *hn = reinterpret_cast<int32_t *>(sl.stage + cur);
@@ -263,8 +311,7 @@ tl_status tl_server::enqueue(Slot &sl, std::vector<Req *> &batch)
         int64_t *hp = hb + nsys;
         const size_t o_n = cur, o_a = cur + up(nsys * 4), o_info = o_a + up(nsys * 24);
         size_t q = 0;
-        for (Req *r : batch) {
-            if (r->d.kind != TL_REQ_SOLVE) continue;
+        for (Req *r : solves) {
             const int64_t n = r->d.n;
             for (int64_t s = 0; s < r->d.count; ++s, ++q) {
                 hn[q] = static_cast<int32_t>(n);
@@ -283,43 +330,24 @@ tl_status tl_server::enqueue(Slot &sl, std::vector<Req *> &batch)
                                    reinterpret_cast<double *>(base), da + 2 * nsys, reinterpret_cast<int32_t *>(base),
                                    dinfo, TL_PREC_FP64, nullptr, st);
         if (ts != TL_OK) return ts;
-        // results of the solves (info from the tick table)
         q = 0;
-        for (Req *r : batch) {
-            if (r->d.kind != TL_REQ_SOLVE) continue;
+        for (Req *r : solves) {
             const size_t c = static_cast<size_t>(r->d.count);
             e = cudaMemcpyAsync(r->d.i2, dinfo + q, c * 4, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = copy_out(r);
             if (e != cudaSuccess) return fail_cuda(sl.h, e);
             q += c;
         }
+        if ((ts = close_group(solves)) != TL_OK) return ts;
     }
-    // outputs
-    for (Req *r : batch) {
-        const size_t c = static_cast<size_t>(r->d.count);
-        if (c == 0) continue;
-        if (r->d.kind == TL_REQ_NEWTON) {
-            e = cudaMemcpyAsync(r->d.x, dptr(r->o_x), c * r->xrows() * 8, cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess && r->has_aux())
-                e = cudaMemcpyAsync(r->d.aux, dptr(r->o_aux), c * 6 * 8, cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(r->d.i1, dptr(r->o_i1), c * 4, cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(r->d.i2, dptr(r->o_i2), c * 4, cudaMemcpyDeviceToHost, st);
-        } else {
-            const size_t n = static_cast<size_t>(r->d.n);
-            e = cudaMemcpyAsync(r->d.x, dptr(r->o_x), c * n * 8, cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(r->d.i1, dptr(r->o_i1), c * n * 4, cudaMemcpyDeviceToHost, st);
-        }
-        if (e != cudaSuccess) return fail_cuda(sl.h, e);
-    }
-    e = cudaEventRecord(sl.ev, st);
-    if (e != cudaSuccess) return fail_cuda(sl.h, e);
     return TL_OK;
 }
 
-// Called with mu held: the slot's tick ended with `status`.
-void tl_server::finish(Slot &sl, int32_t status)
+// Called with mu held: one group of a tick ended with `status`.
+void tl_server::finish_group(Slot &, Group &g, int32_t status)
 {
     const Clock::time_point now = Clock::now();
-    for (Req *r : sl.reqs) {
+    for (Req *r : g.reqs) {
         r->done = true;
         r->status = status;
         r->t_done = now;
@@ -332,11 +360,37 @@ void tl_server::finish(Slot &sl, int32_t status)
             ++stats.failed;
         }
     }
+    g.done = true;
+    cv_done.notify_all();
+}
+
+// Called with mu held: finish the groups whose events completed (all of
+// them, with `failed` for the requests no group recorded, when failed is
+// not TL_OK and the stream has drained); free the slot when none is left.
+void tl_server::retire(Slot &sl, tl_status failed)
+{
+    for (size_t g = 0; g < sl.groups.size(); ++g) {
+        Group &gr = sl.groups[g];
+        if (gr.done) continue;
+        const cudaError_t q = cudaEventQuery(sl.evs[g]);
+        if (q == cudaErrorNotReady) return;  // later groups are behind it on the stream
+        if (q != cudaSuccess) {
+            cudaGetLastError();
+            h->last_cuda_error = static_cast<int>(q);
+        }
+        finish_group(sl, gr, q == cudaSuccess ? TL_OK : TL_ERR_CUDA);
+    }
+    if (failed != TL_OK) {
+        Group rest;
+        for (Req *r : sl.reqs)
+            if (!r->done) rest.reqs.push_back(r);
+        if (!rest.reqs.empty()) finish_group(sl, rest, failed);
+    }
     if (sl.scratch_off != SIZE_MAX) arena.release(sl.scratch_off, sl.scratch_bytes);
     sl.scratch_off = SIZE_MAX;
     sl.reqs.clear();
+    sl.groups.clear();
     sl.busy = false;
-    cv_done.notify_all();
 }
 
 void tl_server::run()
@@ -348,16 +402,8 @@ void tl_server::run()
         bool any_busy = false;
         for (Slot &sl : slots) {
             if (!sl.busy) continue;
-            const cudaError_t q = cudaEventQuery(sl.ev);
-            if (q == cudaErrorNotReady) {
-                any_busy = true;
-                continue;
-            }
-            if (q != cudaSuccess) {
-                cudaGetLastError();
-                h->last_cuda_error = static_cast<int>(q);
-            }
-            finish(sl, q == cudaSuccess ? TL_OK : TL_ERR_CUDA);
+            retire(sl, TL_OK);
+            if (sl.busy) any_busy = true;
         }
         if (stop && pending.empty() && !any_busy) break;
         // admit the head of the queue into a free slot
@@ -386,7 +432,7 @@ void tl_server::run()
                     // whatever was issued drains before the slot is reused
                     cudaStreamSynchronize(sl.stream);
                     cudaGetLastError();
-                    finish(sl, ts);
+                    retire(sl, ts);
                 }
                 launched = true;
             } else if (!any_busy) {
@@ -429,8 +475,13 @@ extern "C" tl_status tl_server_create(tl_handle *h, const tl_server_config *cfg,
     s->arena.reset(cfg->budget_bytes);
     s->slots.resize(static_cast<size_t>(cfg->slots));
     for (Slot &sl : s->slots) {
-        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess || tl_create(&sl.h) != TL_OK) {
+        bool ok = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess && tl_create(&sl.h) == TL_OK;
+        for (int g = 0; ok && g < kMaxGroups; ++g) {
+            cudaEvent_t ev = nullptr;
+            ok = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+            if (ok) sl.evs.push_back(ev);
+        }
+        if (!ok) {
             cudaGetLastError();
             tl_server_destroy(s);
             return TL_ERR_CUDA;
@@ -528,7 +579,7 @@ extern "C" tl_status tl_server_destroy(tl_server *s)
     if (s->loop.joinable()) s->loop.join();
     for (Slot &sl : s->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
-        if (sl.ev) cudaEventDestroy(sl.ev);
+        for (cudaEvent_t ev : sl.evs) cudaEventDestroy(ev);
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.h) tl_destroy(sl.h);
         if (sl.stage) cudaFreeHost(sl.stage);

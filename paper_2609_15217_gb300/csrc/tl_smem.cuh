@@ -121,14 +121,29 @@ __global__ void __launch_bounds__(128) k_smem_group(SolveArgs args, int n)
     bool tiny = false;
     const int wcols = n + (MODE == kGesv ? 1 : 0);         // columns incl. b
     for (int k = 0; k < n; ++k) {
-        // a2: first maximum of |a_ik| over positions k..n-1
+        // a2: first maximum of |a_ik| over positions k..hi-1: the whole
+        // column, or with tile-local pivoting the diagonal tile first and
+        // the positions below it only when the tile's best magnitude is
+        // under the threshold (the first maximum over k..n-1 then)
+        int hi = n;
+        if (args.tile > 0 && args.tile < n) hi = min(n, (k / args.tile + 1) * args.tile);
         double cv = 0.0;
         int cpos = n;
-        for (int i = k + t; i < n; i += T) {
+        for (int i = k + t; i < hi; i += T) {
             const double v = M[perm[i] * RS + k];
             if (cpos == n || dev::mag_bits(v) > dev::mag_bits(cv)) { cv = v; cpos = i; }
         }
         dev::group_argmax<T>(cv, cpos);
+        if (hi < n) {
+            const bool below = dev::mag_bits(cv) < dev::mag_bits(args.threshold);
+            if (below) {
+                for (int i = hi + ((t - hi) % T + T) % T; i < n; i += T) {
+                    const double v = M[perm[i] * RS + k];
+                    if (dev::mag_bits(v) > dev::mag_bits(cv)) { cv = v; cpos = i; }
+                }
+            }
+            if (__any_sync(0xffffffffu, below)) dev::group_argmax<T>(cv, cpos);
+        }
         const int p = cpos;
         const bool zero = dev::mag_bits(cv) == 0ULL;
         if (zero && info == 0) info = k + 1;

@@ -68,6 +68,8 @@ _SIGS = {
                                      _int, _vp], _int),
     "tl_newton_integrate_cpu_driven": ([_vp, C.POINTER(tl_law), _i64, _vp, _vp, _vp, _vp, _vp, C.c_double, _int,
                                         _vp], _int),
+    "tl_gesv_batched_tilepiv": ([_vp, _int, _int, C.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _int, _i64, _i64, _vp],
+                                _int),
     "tl_autotune": ([_vp, _int, _int, _int, C.c_char_p], _int),
     "tl_server_create": ([_vp, C.POINTER(tl_server_config), C.POINTER(_vp)], _int),
     "tl_server_submit": ([_vp, C.POINTER(tl_request), C.POINTER(_i64)], _int),
@@ -206,6 +208,12 @@ def tl_newton_integrate_cpu_driven(h, law, npoints, inputs, x, outputs, iteratio
                                    stream=None):
     return _lib.tl_newton_integrate_cpu_driven(h, C.byref(law), npoints, _p(inputs), _p(x), _p(outputs),
                                                _p(iterations), _p(status), rtol, max_iter, _stream(stream))
+
+
+def tl_gesv_batched_tilepiv(h, n, tile, threshold, A, LU_out, b, x, ipiv, info, layout, ld_batch, batch,
+                            stream=None):
+    return _lib.tl_gesv_batched_tilepiv(h, n, tile, threshold, _p(A), _p(LU_out), _p(b), _p(x), _p(ipiv), _p(info),
+                                        layout, ld_batch, batch, _stream(stream))
 
 
 def tl_autotune(h, n_min, n_max, layout, table_path=None):
