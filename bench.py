@@ -667,6 +667,8 @@ def main():
     ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="force one kernel variant (lanes + 100 * storage) for every n of the sweep")
     ap.add_argument("--dispatch-table", default=None,
                     help="interleaved-layout dispatch table (JSON written by tl_autotune) to apply instead of "
                          "autotuning, e.g. to profile the same kernels the timed run used")
@@ -700,7 +702,11 @@ def main():
     h = tl.tl_create()
     n_list = list(range(args.nmin, args.nmax + 1))
     tune = {}
-    if args.dispatch_table:
+    if args.variant is not None:
+        for n in range(args.nmin, args.nmax + 1):
+            tl.check("tl_dispatch_set", tl.tl_dispatch_set(h, n, 1, args.variant, 0), h)
+        tune[1] = {n: args.variant for n in range(args.nmin, args.nmax + 1)}
+    elif args.dispatch_table:
         with open(args.dispatch_table) as f:
             entries = json.load(f)["entries"]
         for e in entries:

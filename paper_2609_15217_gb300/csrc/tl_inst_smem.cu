@@ -22,10 +22,12 @@ struct SmemRegistrar {
         reg_smem<4, kPerSystem>();
         reg_smem<8, kPerSystem>();
         reg_smem<16, kPerSystem>();
+        reg_smem<32, kPerSystem>();
         reg_smem<2, kInterleaved>();
         reg_smem<4, kInterleaved>();
         reg_smem<8, kInterleaved>();
         reg_smem<16, kInterleaved>();
+        reg_smem<32, kInterleaved>();
     }
 };
 const SmemRegistrar smem_registrar_instance;

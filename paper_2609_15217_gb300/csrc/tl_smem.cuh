@@ -2,19 +2,18 @@
 // system, run-time n (<= 32).
 //
 // Each system is an augmented n x (n+1) row-major block in shared memory
-// (column n holds b, then y, then x).  Rows are never moved: a position ->
-// row table `perm` implements the physical interchanges of Sec. 2.2 (swapping
-// two table entries swaps two whole rows, L part included), and a pivot
-// candidate at position i is the row perm[i], so the first-maximum rule sees
-// exactly the row order of the sequential algorithm.
+// (column n holds b, then y, then x), rows RS doubles apart.  The
+// interchanges of Sec. 2.2 swap whole rows (L part included) in place, the
+// T lanes sharing the columns.
 //
 // Work split: at elimination step k the m = n-k-1 live rows and the n-k live
-// columns (b included) form one flattened block of m(n-k) updates that the T
-// lanes share element by element, so every FP64 instruction issued at a step
-// is useful except for the last partial round of each lane: the lane
-// efficiency stays near 1 at every step, unlike a row-cyclic split whose
-// dead rows keep their slots issued.  All loops run at run time, so the code
-// is small and stays in the instruction cache whatever n is.
+// columns (b included) are cut among a TR x TC tile of lanes (4 x 4 for
+// T = 16): lane (tr, tc) keeps its columns of the pivot row in registers and
+// walks its rows, one multiplier per row, so an update costs one shared
+// load and one store; every lane has the same number of live elements up to
+// one row or column.  The column loop stops at a bound that is the same for
+// the whole warp, so no FP64 instruction is issued for a dead column chunk.
+// Loops over rows run at run time, so the code stays small whatever n is.
 //
 // Arithmetic is the same as the register solvers of tl_device.cuh (negated
 // multipliers a_ik * (-RN(1/a_kk)), one FMA per update in increasing k, the
@@ -26,13 +25,19 @@
 
 namespace tl {
 
-// Shared-memory footprint of one system in doubles: the n x (n+1) block,
-// 32 reciprocals, 32 + 32 ints (row table, pivots).  Padded so that the
-// systems of one half-warp (16 lanes of 8-byte accesses) start T banks apart
-// and their lanes do not collide on the same bank.
+// Row stride of a system's n x (n+1) block: the smallest odd number of
+// doubles >= n+1, so that a column walked by consecutive lanes hits distinct
+// banks and the block stays small (shared memory bounds the warps resident
+// per SM).
+__host__ __device__ constexpr int smem_row_stride(int n) { return (n + 1) | 1; }
+
+// Shared-memory footprint of one system in doubles: the n x RS block, 32
+// reciprocals, 32 pivots (16 doubles).  Padded so that consecutive systems
+// start T slots apart modulo 16 (the systems of one half-warp then do not
+// collide on a bank).
 __host__ __device__ constexpr int smem_sys_doubles(int n, int T = 16)
 {
-    const int base = n * (n + 1) + 32 + 32;
+    const int base = n * smem_row_stride(n) + 32 + 16;
     const int want = (T < 16) ? T : 0;
     return base + ((want - base % 16) % 16 + 16) % 16;
 }
@@ -56,7 +61,7 @@ __global__ void __launch_bounds__(128) k_smem_group(SolveArgs args, int n)
     extern __shared__ double smem[];
     const int SB = blockDim.x / T;                 // systems per block
     const int per = smem_sys_doubles(n, T);
-    const int RS = n + 1;                          // row stride
+    const int RS = smem_row_stride(n);            // row stride
     const int64_t s0 = static_cast<int64_t>(blockIdx.x) * SB;
     const double *Ag = (MODE == kGetrf) ? args.LU : args.A;
     const int nn = n * n;
@@ -101,36 +106,41 @@ __global__ void __launch_bounds__(128) k_smem_group(SolveArgs args, int n)
     __syncthreads();
 
     // ---- compute: lanes t = lane % T of a group own system q ----
+    // Trailing updates use a TR x TC tile of lanes: lane (tr, tc) updates
+    // rows k+1+tr, k+1+tr+TR, ... and columns k+1+tc, k+1+tc+TC, ...,
+    // keeping its columns of the pivot row in registers.
+    constexpr int TC = (T >= 4) ? 4 : T;
+    constexpr int TR = T / TC;
+    constexpr int MAXC = TL_MAX_N / TC;  // whole column chunks per lane (at most 32 live columns)
+    static_assert(MAXC <= 16, "the chunk switch below covers 16 chunks");
     const int lane = threadIdx.x & 31;
     const int t = lane % T;
+    const int tr = t / TC, tc = t % TC;
     const int q = threadIdx.x / T;
     const int64_t s = s0 + q;
     const bool active = s < args.batch;
     double *M = smem + q * per;
     double *rcp = M + n * RS;                              // 32 doubles
-    int *perm = reinterpret_cast<int *>(rcp + 32);         // 32 ints
-    int *piv = perm + 32;                                  // 32 ints
+    int *piv = reinterpret_cast<int *>(rcp + 32);          // 32 ints
     // non-finite entries anywhere in this system (loaded by threads q + SB*t')
     int badv = 0;
     for (int tp = t; tp < T; tp += T) badv |= s_bad[q + SB * tp];
     const bool bad = group_any_int<T>(badv) != 0;
-    for (int i = t; i < n; i += T) perm[i] = i;
-    __syncwarp();
 
     int info = 0;
     bool tiny = false;
     const int wcols = n + (MODE == kGesv ? 1 : 0);         // columns incl. b
     for (int k = 0; k < n; ++k) {
-        // a2: first maximum of |a_ik| over positions k..hi-1: the whole
-        // column, or with tile-local pivoting the diagonal tile first and
-        // the positions below it only when the tile's best magnitude is
-        // under the threshold (the first maximum over k..n-1 then)
+        // a2: first maximum of |a_ik| over rows k..hi-1: the whole column,
+        // or with tile-local pivoting the diagonal tile first and the rows
+        // below it only when the tile's best magnitude is under the
+        // threshold (the first maximum over k..n-1 then)
         int hi = n;
         if (args.tile > 0 && args.tile < n) hi = min(n, (k / args.tile + 1) * args.tile);
         double cv = 0.0;
         int cpos = n;
         for (int i = k + t; i < hi; i += T) {
-            const double v = M[perm[i] * RS + k];
+            const double v = M[i * RS + k];
             if (cpos == n || dev::mag_bits(v) > dev::mag_bits(cv)) { cv = v; cpos = i; }
         }
         dev::group_argmax<T>(cv, cpos);
@@ -138,7 +148,7 @@ __global__ void __launch_bounds__(128) k_smem_group(SolveArgs args, int n)
             const bool below = dev::mag_bits(cv) < dev::mag_bits(args.threshold);
             if (below) {
                 for (int i = hi + ((t - hi) % T + T) % T; i < n; i += T) {
-                    const double v = M[perm[i] * RS + k];
+                    const double v = M[i * RS + k];
                     if (dev::mag_bits(v) > dev::mag_bits(cv)) { cv = v; cpos = i; }
                 }
             }
@@ -148,15 +158,15 @@ __global__ void __launch_bounds__(128) k_smem_group(SolveArgs args, int n)
         const bool zero = dev::mag_bits(cv) == 0ULL;
         if (zero && info == 0) info = k + 1;
         if (t == 0) piv[k] = p;
-        __syncwarp();
-        // a3: interchange positions k and p (whole rows, L part included)
-        if (t == 0 && p != k) {
-            const int tmp = perm[k];
-            perm[k] = perm[p];
-            perm[p] = tmp;
+        // a3: physical interchange of rows k and p (L part and b included)
+        if (p != k) {
+            for (int j = t; j < wcols; j += T) {
+                const double tmp = M[k * RS + j];
+                M[k * RS + j] = M[p * RS + j];
+                M[p * RS + j] = tmp;
+            }
         }
         __syncwarp();
-        const int rk = perm[k];
         // a4: reciprocal and negated multipliers
         const bool small = !zero && dev::mag_bits(cv) < dev::kDblMinBits;
         const double r = dev::rcp_rn(cv);
@@ -165,48 +175,60 @@ __global__ void __launch_bounds__(128) k_smem_group(SolveArgs args, int n)
         const double nr = dev::neg(r);
         if (!__any_sync(0xffffffffu, small)) {
             for (int i = k + 1 + t; i < n; i += T) {
-                double *a = &M[perm[i] * RS + k];
+                double *a = &M[i * RS + k];
                 *a = zero ? dev::neg(*a) : __dmul_rn(*a, nr);
             }
         } else {
             const double ncv = dev::neg(cv);
             for (int i = k + 1 + t; i < n; i += T) {
-                double *a = &M[perm[i] * RS + k];
+                double *a = &M[i * RS + k];
                 *a = zero ? dev::neg(*a) : (small ? __ddiv_rn(*a, ncv) : __dmul_rn(*a, nr));
             }
         }
         __syncwarp();
-        // a5 (+ forward part of a6 through column n): a_ij += (-l_ik) u_kj
+        // a5 (+ forward part of a6 through column n): a_ij += (-l_ik) u_kj.
+        // Lane (tr, tc) owns columns k+1+tc + c*TC: nfull whole chunks
+        // (the same count on every lane of the warp) and possibly one tail
+        // column; the chunks are a straight-line fall-through block entered
+        // once per row, with immediate offsets from the row pointer.
         if (!zero) {
-            const int m = n - k - 1;
-            const int w = wcols - k - 1;
-            const int total = m * w;
-            if (total > 0) {
-                // each lane walks elements e = t, t+T, ... of the flattened
-                // m x w block, four at a time: all loads of a group are issued
-                // before its FMAs (the four elements are distinct, so the
-                // reordering is exact; the compiler cannot prove it alone)
-                int ii = t / w, jj = t % w;
-                const double *urow = M + rk * RS + k + 1;
-                for (int e = t; e < total; e += 4 * T) {
-                    int off[4];
-                    double l[4], u[4], a[4];
+            const int ncols = wcols - (k + 1);
+            const int nfull = ncols / TC;
+            const bool has_tail = tc < ncols - nfull * TC;
+            const double *urow = M + k * RS + k + 1 + tc;
+            double u[MAXC];
 #pragma unroll
-                    for (int q2 = 0; q2 < 4; ++q2) {
-                        const bool ok = e + q2 * T < total;
-                        const int row = ok ? perm[k + 1 + ii] : rk;
-                        off[q2] = ok ? row * RS + k + 1 + jj : -1;
-                        l[q2] = ok ? M[row * RS + k] : 0.0;
-                        u[q2] = ok ? urow[jj] : 0.0;
-                        jj += T;
-                        while (jj >= w) { jj -= w; ++ii; }
-                    }
-#pragma unroll
-                    for (int q2 = 0; q2 < 4; ++q2) a[q2] = off[q2] >= 0 ? M[off[q2]] : 0.0;
-#pragma unroll
-                    for (int q2 = 0; q2 < 4; ++q2)
-                        if (off[q2] >= 0) M[off[q2]] = __fma_rn(l[q2], u[q2], a[q2]);
+            for (int c = 0; c < MAXC; ++c) u[c] = c < nfull ? urow[c * TC] : 0.0;
+            const double ut = has_tail ? urow[nfull * TC] : 0.0;
+            for (int i = k + 1 + tr; i < n; i += TR) {
+                double *Mi = M + i * RS;
+                const double l = Mi[k];
+                double *Mr = Mi + k + 1 + tc;
+                switch (nfull) {
+#define TL_SMEM_CHUNK(c)                                                                \
+    case (c) + 1:                                                                       \
+        if ((c) < MAXC) Mr[(c) * TC] = __fma_rn(l, u[(c) < MAXC ? (c) : 0], Mr[(c) * TC]); \
+        [[fallthrough]];
+                    TL_SMEM_CHUNK(15)
+                    TL_SMEM_CHUNK(14)
+                    TL_SMEM_CHUNK(13)
+                    TL_SMEM_CHUNK(12)
+                    TL_SMEM_CHUNK(11)
+                    TL_SMEM_CHUNK(10)
+                    TL_SMEM_CHUNK(9)
+                    TL_SMEM_CHUNK(8)
+                    TL_SMEM_CHUNK(7)
+                    TL_SMEM_CHUNK(6)
+                    TL_SMEM_CHUNK(5)
+                    TL_SMEM_CHUNK(4)
+                    TL_SMEM_CHUNK(3)
+                    TL_SMEM_CHUNK(2)
+                    TL_SMEM_CHUNK(1)
+                    TL_SMEM_CHUNK(0)
+#undef TL_SMEM_CHUNK
+                default: break;
                 }
+                if (has_tail) Mr[nfull * TC] = __fma_rn(l, ut, Mr[nfull * TC]);
             }
         }
         __syncwarp();
@@ -216,20 +238,16 @@ __global__ void __launch_bounds__(128) k_smem_group(SolveArgs args, int n)
     if (MODE == kGesv) {
         const bool any_tiny = __any_sync(0xffffffffu, tiny);
         for (int i = n - 1; i >= 0; --i) {
-            const int ri = perm[i];
             if (t == 0) {
-                const double y = M[ri * RS + n];
+                const double y = M[i * RS + n];
                 double xi;
                 if (!any_tiny) xi = __dmul_rn(y, rcp[i]);
-                else xi = tiny ? __ddiv_rn(y, M[ri * RS + i]) : __dmul_rn(y, rcp[i]);
-                M[ri * RS + n] = xi;
+                else xi = tiny ? __ddiv_rn(y, M[i * RS + i]) : __dmul_rn(y, rcp[i]);
+                M[i * RS + n] = xi;
             }
             __syncwarp();
-            const double nxi = dev::neg(M[ri * RS + n]);
-            for (int r2 = t; r2 < i; r2 += T) {
-                const int rr = perm[r2];
-                M[rr * RS + n] = __fma_rn(M[rr * RS + i], nxi, M[rr * RS + n]);
-            }
+            const double nxi = dev::neg(M[i * RS + n]);
+            for (int r2 = t; r2 < i; r2 += T) M[r2 * RS + n] = __fma_rn(M[r2 * RS + i], nxi, M[r2 * RS + n]);
             __syncwarp();
         }
     }
@@ -239,17 +257,17 @@ __global__ void __launch_bounds__(128) k_smem_group(SolveArgs args, int n)
     if (active) {
         for (int i = t; i < n; i += T) {
             const int64_t vi = (LAYOUT == kInterleaved) ? static_cast<int64_t>(i) * args.ld + s : s * n + i;
-            if (MODE == kGesv) st_stream(args.x + vi, info != 0 ? dev::nan_value() : M[perm[i] * RS + n]);
+            if (MODE == kGesv) st_stream(args.x + vi, info != 0 ? dev::nan_value() : M[i * RS + n]);
             st_stream(args.ipiv + vi, bad ? i + 1 : piv[i] + 1);
         }
         if (t == 0) st_stream(args.info + s, info);
         if (KEEP) {
-            // element e = j*n + i of the factors: row at position i, column j
+            // element e = j*n + i of the factors
             for (int e = t; e < nn; e += T) {
                 const int i = e % n, j = e / n;
                 const int64_t ai = (LAYOUT == kInterleaved) ? static_cast<int64_t>(e) * args.ld + s : s * nn + e;
                 if (!bad) {
-                    const double v = M[perm[i] * RS + j];
+                    const double v = M[i * RS + j];
                     st_stream(args.LU + ai, j < i ? dev::neg(v) : v);
                 } else if (MODE == kGesv) {
                     args.LU[ai] = args.A[ai];

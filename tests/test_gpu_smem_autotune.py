@@ -34,7 +34,7 @@ def h(tl):
     tl.tl_destroy(hh)
 
 
-@pytest.mark.parametrize("lanes", [2, 4, 8, 16])
+@pytest.mark.parametrize("lanes", [2, 4, 8, 16, 32])
 @pytest.mark.parametrize("n", [2, 3, 7, 9, 10, 13, 16, 17, 24, 25, 31, 32])
 def test_shared_memory_variants(tl, h, n, lanes):
     batch = 3 * 64 + 11
