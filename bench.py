@@ -83,10 +83,15 @@ def bytes_per_system(n):
 FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12
 
 
-# DRAM bytes per system measured by ncu for the current kernels
-# (dram__bytes_read.sum + dram__bytes_write.sum of one launch / systems);
-# an entry must be removed whenever its kernel changes.
-DRAM_BYTES_PER_SYSTEM = {}
+# DRAM bytes per system measured by ncu for the current kernels, keyed by
+# (variant, n) (dram__bytes_read.sum + dram__bytes_write.sum of one launch /
+# systems); an entry must be removed whenever its kernel changes.
+DRAM_BYTES_PER_SYSTEM = {(132, 32): 8786}
+
+VARIANT_NAMES = {1: "k_factor_thread", 2: "k_factor_group<T=2>", 4: "k_factor_group<T=4>",
+                 8: "k_factor_group<T=8>", 16: "k_factor_group<T=16>", 102: "k_smem_group<T=2>",
+                 104: "k_smem_group<T=4>", 108: "k_smem_group<T=8>", 116: "k_smem_group<T=16>",
+                 132: "k_smem_group<T=32>"}
 
 
 def load_peaks():
@@ -745,19 +750,30 @@ def main():
                         "fp64_tflops": f / (ms / 1e3) / 1e12,
                         "fp64_frac": f / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
                         "gbs": bytes_per_system(n) * d["S"] / (ms / 1e3) / 1e9}
-    dom = max(per_n_out, key=lambda n: per_n_out[n]["ms"])
-    if 32 in per_n_out and per_n_out[32]["ms"] >= 0.97 * per_n_out[dom]["ms"]:
-        dom = 32  # the n=25..32 launches take equal shares; n=32 is the profiled one
+    # dominant kernel: the variant (thread-to-system mapping + storage) with
+    # the largest share of the step; its largest launch is the roofline unit
+    variant_of = {n: tl.tl_dispatch_get(h, n, 1)[1] for n in per_n_out}
+    fam_ms = {}
+    for n, v in variant_of.items():
+        fam_ms[v] = fam_ms.get(v, 0.0) + per_n_out[n]["ms"]
+    fam = max(fam_ms, key=fam_ms.get)
+    fam_n = sorted(n for n in per_n_out if variant_of[n] == fam)
+    dom = max(fam_n, key=lambda n: per_n_out[n]["ms"])
     dom_flops = flops_per_system(dom) * data[dom]["S"]
     achieved = dom_flops / (per_n_out[dom]["ms"] / 1e3) / 1e12
-    traffic = DRAM_BYTES_PER_SYSTEM.get(dom)
-    roofline = {"bound": "alu", "pipe": "fp64", "kernel": f"gesv n={dom} interleaved",
+    fam_flops = sum(flops_per_system(n) * data[n]["S"] for n in fam_n)
+    traffic = DRAM_BYTES_PER_SYSTEM.get((fam, dom))
+    roofline = {"bound": "alu", "pipe": "fp64",
+                "kernel": f"{VARIANT_NAMES.get(fam, fam)} (variant {fam}), gesv n={dom} interleaved launch",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": traffic * data[dom]["S"] if traffic else None,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per system, scaled to the launch"
-                if traffic else None,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per system on a smaller batch "
+                                  "of the same kernel and n, scaled to the launch" if traffic else None,
                 "peak_source": "derived: 152 SMs x 4 SMSPs x 0.5 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25)",
+                "kernel_share_of_step": fam_ms[fam] / sum(fam_ms.values()),
+                "kernel_n": fam_n,
+                "kernel_fp64_frac": fam_flops / (fam_ms[fam] / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
                 "sweep_fp64_frac": flops_total / (med_step / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
     del data
     torch.cuda.empty_cache()
