@@ -55,6 +55,12 @@ int default_ir_lanes(int n)
     return 16;
 }
 
+int default_ragged_id(int n)
+{
+    if (n <= 16) return default_lanes(n);
+    return variant_id(n <= 26 ? 16 : 32, 1);
+}
+
 // Default variant id per n before any autotuning.
 int default_lanes(int n) { return variant_id(default_register_lanes(n), 0); }
 
@@ -85,7 +91,7 @@ tl_status fail_cuda(tl_handle *h, cudaError_t e)
 
 // Resident blocks per SM of `kernel` at `block` threads and `smem` bytes of
 // dynamic shared memory (cached).
-static int blocks_per_sm(tl_handle *h, const void *kernel, int block, size_t smem)
+int blocks_per_sm(tl_handle *h, const void *kernel, int block, size_t smem)
 {
     auto key = std::make_pair(kernel, block * 1048576 + static_cast<int>(smem / 16));
     auto it = h->occupancy.find(key);
@@ -128,6 +134,27 @@ int pick_block(tl_handle *h, const void *kernel, int64_t threads, int lanes, siz
     return best;
 }
 
+// Allow a shared-memory kernel all the opt-in shared memory its static part
+// leaves free (once per kernel, before any occupancy query); *limit receives
+// the dynamic shared memory a block may use.
+tl_status smem_opt_in(tl_handle *h, const void *kernel, int *limit)
+{
+    auto it = h->smem_opt_in.find(kernel);
+    if (it != h->smem_opt_in.end()) {
+        *limit = it->second;
+        return TL_OK;
+    }
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    const int dyn_limit = h->max_smem_per_block - static_cast<int>(fa.sharedSizeBytes);
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_limit);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    h->smem_opt_in[kernel] = dyn_limit;
+    *limit = dyn_limit;
+    return TL_OK;
+}
+
 tl_status launch_variant(tl_handle *h, const Variant *v, int n, int block, SolveArgs &args, cudaStream_t stream)
 {
     if (args.batch == 0) return TL_OK;
@@ -136,20 +163,8 @@ tl_status launch_variant(tl_handle *h, const Variant *v, int n, int block, Solve
     cudaError_t e;
     int dyn_limit = h->max_smem_per_block;
     if (v->kind == 1) {
-        auto it = h->smem_opt_in.find(v->kernel);
-        if (it == h->smem_opt_in.end()) {
-            // allow all the opt-in shared memory the static part leaves free,
-            // before any occupancy query
-            cudaFuncAttributes fa;
-            e = cudaFuncGetAttributes(&fa, v->kernel);
-            if (e != cudaSuccess) return fail_cuda(h, e);
-            dyn_limit = h->max_smem_per_block - static_cast<int>(fa.sharedSizeBytes);
-            e = cudaFuncSetAttribute(v->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_limit);
-            if (e != cudaSuccess) return fail_cuda(h, e);
-            h->smem_opt_in[v->kernel] = dyn_limit;
-        } else {
-            dyn_limit = it->second;
-        }
+        const tl_status st = smem_opt_in(h, v->kernel, &dyn_limit);
+        if (st != TL_OK) return st;
     }
     if (block <= 0) block = pick_block(h, v->kernel, threads, v->lanes, per_sys, dyn_limit);
     const int64_t grid = (threads + block - 1) / block;

@@ -35,6 +35,11 @@ tl_status fail_cuda(tl_handle *h, cudaError_t e);
 int pick_block(tl_handle *h, const void *kernel, int64_t threads, int lanes, size_t smem_per_system,
                int smem_limit);
 tl_status launch_variant(tl_handle *h, const Variant *v, int n, int block, SolveArgs &args, cudaStream_t stream);
+tl_status smem_opt_in(tl_handle *h, const void *kernel, int *limit);
+int blocks_per_sm(tl_handle *h, const void *kernel, int block, size_t smem);
+// Default ragged variant id for n: register kernels up to n = 16, the
+// shared-memory solver (16 lanes, then 32) above.
+int default_ragged_id(int n);
 tl_status launch_op(tl_handle *h, int n, int layout, int op, SolveArgs &args, cudaStream_t stream);
 tl_status ensure_workspace(tl_handle *h, size_t bytes, cudaStream_t stream);
 // Buckets `batch` systems by n[s] using the int32 scratch `ws` (3*64 bin

@@ -15,6 +15,13 @@ void reg_smem()
     }
 }
 
+template <int T>
+void reg_smem_ragged()
+{
+    for (int n = 2; n <= TL_MAX_N; ++n)
+        register_variant(n, kPerSystem, kOpRagged, T, reinterpret_cast<const void *>(&k_smem_ragged<T>), 1);
+}
+
 struct SmemRegistrar {
     SmemRegistrar()
     {
@@ -28,6 +35,9 @@ struct SmemRegistrar {
         reg_smem<8, kInterleaved>();
         reg_smem<16, kInterleaved>();
         reg_smem<32, kInterleaved>();
+        reg_smem_ragged<8>();
+        reg_smem_ragged<16>();
+        reg_smem_ragged<32>();
     }
 };
 const SmemRegistrar smem_registrar_instance;

@@ -11,6 +11,7 @@
 #include "tinylu.h"
 #include "tl_handle.h"
 #include "tl_internal.h"
+#include "tl_smem.cuh"
 
 namespace tl {
 namespace {
@@ -124,14 +125,45 @@ unsigned ragged_grid(tl_handle *h, const Variant *v, int64_t batch, int blk)
     return static_cast<unsigned>(need < resident ? need : resident);
 }
 
+// Persistent launch of a shared-memory ragged kernel for size nn.
+tl_status launch_smem_ragged(tl_handle *h, const Variant *v, int nn, int64_t batch, RaggedArgs &r,
+                             cudaStream_t stream)
+{
+    int limit = 0;
+    tl_status st = smem_opt_in(h, v->kernel, &limit);
+    if (st != TL_OK) return st;
+    const size_t per = smem_sys_bytes(nn, v->lanes);
+    for (int blk : {128, 64, 32}) {
+        if (blk < v->lanes) continue;
+        const size_t smem = static_cast<size_t>(blk / v->lanes) * per;
+        if (smem > static_cast<size_t>(limit)) continue;
+        const int nb = blocks_per_sm(h, v->kernel, blk, smem);
+        if (nb < 1) continue;
+        const int64_t sb = blk / v->lanes;
+        const int64_t need = (batch + sb - 1) / sb;
+        const int64_t resident = static_cast<int64_t>(nb) * h->sm_count;
+        const unsigned g = static_cast<unsigned>(need < resident ? need : resident);
+        int n_arg = nn;
+        void *params[] = {&r, &n_arg};
+        const cudaError_t e = cudaLaunchKernel(v->kernel, dim3(g), dim3(blk), params, smem, stream);
+        if (e != cudaSuccess) return fail_cuda(h, e);
+        return TL_OK;
+    }
+    return TL_ERR_UNSUPPORTED;
+}
+
 // Binary64 ragged kernels for every n over the lists in r.
 tl_status launch_binary64(tl_handle *h, int64_t batch, RaggedArgs &r, cudaStream_t stream)
 {
     for (int nn = 1; nn <= TL_MAX_N; ++nn) {
         const Choice &c = h->choice[nn][kPerSystem][kOpRagged];
-        const Variant *v = find_variant(nn, kPerSystem, kOpRagged, c.lanes ? c.lanes : default_lanes(nn));
-        // (ragged launches use the register kernels only)
+        const Variant *v = find_variant(nn, kPerSystem, kOpRagged, c.lanes ? c.lanes : default_ragged_id(nn));
         if (!v) return TL_ERR_UNSUPPORTED;
+        if (v->kind == 1) {
+            const tl_status st = launch_smem_ragged(h, v, nn, batch, r, stream);
+            if (st != TL_OK) return st;
+            continue;
+        }
         const int blk = 128;
         const unsigned g = ragged_grid(h, v, batch, blk);
         void *params[] = {&r};

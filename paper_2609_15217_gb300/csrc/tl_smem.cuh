@@ -54,79 +54,29 @@ __device__ __forceinline__ int group_any_int(int v)
     return v;
 }
 
-// MODE: kGesv (A const, b -> x, LU optional by KEEP) or kGetrf (A in place).
-template <int T, int LAYOUT, int MODE, bool KEEP>
-__global__ void __launch_bounds__(128) k_smem_group(SolveArgs args, int n)
+// Elimination of one system held by the T lanes of a group: the augmented
+// n x (n+1) block M (row stride RS; column n = b when SOLVE), followed by
+// 32 reciprocals and 32 pivot rows.  LUpp with the arithmetic of the
+// register solvers (negated multipliers a_ik * (-RN(1/a_kk)), one FMA per
+// update in increasing k, b carried as column n, back substitution by
+// RN(1/u_ii)); on return M holds L (negated, below the diagonal) and U, and
+// column n holds x when SOLVE.  Returns info.  Every lane of the warp must
+// call it together (shuffles and votes inside).
+//
+// Trailing updates use a TR x TC tile of lanes: lane (tr, tc) updates
+// rows k+1+tr, k+1+tr+TR, ... and columns k+1+tc, k+1+tc+TC, ..., keeping
+// its columns of the pivot row in registers.
+template <int T, bool SOLVE>
+__device__ __forceinline__ int smem_lupp(double *M, int n, int RS, int t, int tile, double threshold)
 {
-    extern __shared__ double smem[];
-    const int SB = blockDim.x / T;                 // systems per block
-    const int per = smem_sys_doubles(n, T);
-    const int RS = smem_row_stride(n);            // row stride
-    const int64_t s0 = static_cast<int64_t>(blockIdx.x) * SB;
-    const double *Ag = (MODE == kGetrf) ? args.LU : args.A;
-    const int nn = n * n;
-    __shared__ int s_bad[128];
-
-    // ---- load: thread (q = tid % SB, t' = tid / SB) copies elements
-    //      e = t', t'+T, ... of system s0+q (coalesced over q) ----
-    {
-        const int q = threadIdx.x % SB;
-        const int tp = threadIdx.x / SB;
-        const int64_t s = s0 + q;
-        double *M = smem + q * per;
-        int bad = 0;
-        if (s < args.batch) {
-            if (LAYOUT == kInterleaved) {
-                int i = tp % n, j = tp / n;
-                for (int e = tp; e < nn; e += T) {
-                    const double v = ld_stream(Ag + static_cast<int64_t>(e) * args.ld + s);
-                    bad |= dev::is_nonfinite(v);
-                    M[i * RS + j] = v;
-                    i += T;
-                    while (i >= n) { i -= n; ++j; }
-                }
-                if (MODE == kGesv)
-                    for (int i2 = tp; i2 < n; i2 += T) M[i2 * RS + n] = ld_stream(args.b + static_cast<int64_t>(i2) * args.ld + s);
-            } else {
-                const double *src = Ag + s * nn;
-                int i = tp % n, j = tp / n;
-                for (int e = tp; e < nn; e += T) {
-                    const double v = ld_stream(src + e);
-                    bad |= dev::is_nonfinite(v);
-                    M[i * RS + j] = v;
-                    i += T;
-                    while (i >= n) { i -= n; ++j; }
-                }
-                if (MODE == kGesv)
-                    for (int i2 = tp; i2 < n; i2 += T) M[i2 * RS + n] = ld_stream(args.b + s * n + i2);
-            }
-        }
-        s_bad[threadIdx.x] = bad;
-    }
-    __syncthreads();
-
-    // ---- compute: lanes t = lane % T of a group own system q ----
-    // Trailing updates use a TR x TC tile of lanes: lane (tr, tc) updates
-    // rows k+1+tr, k+1+tr+TR, ... and columns k+1+tc, k+1+tc+TC, ...,
-    // keeping its columns of the pivot row in registers.
+    constexpr int MODE = SOLVE ? kGesv : kGetrf;
     constexpr int TC = (T >= 4) ? 4 : T;
     constexpr int TR = T / TC;
     constexpr int MAXC = TL_MAX_N / TC;  // whole column chunks per lane (at most 32 live columns)
     static_assert(MAXC <= 16, "the chunk switch below covers 16 chunks");
-    const int lane = threadIdx.x & 31;
-    const int t = lane % T;
     const int tr = t / TC, tc = t % TC;
-    const int q = threadIdx.x / T;
-    const int64_t s = s0 + q;
-    const bool active = s < args.batch;
-    double *M = smem + q * per;
     double *rcp = M + n * RS;                              // 32 doubles
     int *piv = reinterpret_cast<int *>(rcp + 32);          // 32 ints
-    // non-finite entries anywhere in this system (loaded by threads q + SB*t')
-    int badv = 0;
-    for (int tp = t; tp < T; tp += T) badv |= s_bad[q + SB * tp];
-    const bool bad = group_any_int<T>(badv) != 0;
-
     int info = 0;
     bool tiny = false;
     const int wcols = n + (MODE == kGesv ? 1 : 0);         // columns incl. b
@@ -136,7 +86,7 @@ __global__ void __launch_bounds__(128) k_smem_group(SolveArgs args, int n)
         // below it only when the tile's best magnitude is under the
         // threshold (the first maximum over k..n-1 then)
         int hi = n;
-        if (args.tile > 0 && args.tile < n) hi = min(n, (k / args.tile + 1) * args.tile);
+        if (tile > 0 && tile < n) hi = min(n, (k / tile + 1) * tile);
         double cv = 0.0;
         int cpos = n;
         for (int i = k + t; i < hi; i += T) {
@@ -145,7 +95,7 @@ __global__ void __launch_bounds__(128) k_smem_group(SolveArgs args, int n)
         }
         dev::group_argmax<T>(cv, cpos);
         if (hi < n) {
-            const bool below = dev::mag_bits(cv) < dev::mag_bits(args.threshold);
+            const bool below = dev::mag_bits(cv) < dev::mag_bits(threshold);
             if (below) {
                 for (int i = hi + ((t - hi) % T + T) % T; i < n; i += T) {
                     const double v = M[i * RS + k];
@@ -251,6 +201,75 @@ __global__ void __launch_bounds__(128) k_smem_group(SolveArgs args, int n)
             __syncwarp();
         }
     }
+    return info;
+}
+
+// MODE: kGesv (A const, b -> x, LU optional by KEEP) or kGetrf (A in place).
+template <int T, int LAYOUT, int MODE, bool KEEP>
+__global__ void __launch_bounds__(128) k_smem_group(SolveArgs args, int n)
+{
+    extern __shared__ double smem[];
+    const int SB = blockDim.x / T;                 // systems per block
+    const int per = smem_sys_doubles(n, T);
+    const int RS = smem_row_stride(n);            // row stride
+    const int64_t s0 = static_cast<int64_t>(blockIdx.x) * SB;
+    const double *Ag = (MODE == kGetrf) ? args.LU : args.A;
+    const int nn = n * n;
+    __shared__ int s_bad[128];
+
+    // ---- load: thread (q = tid % SB, t' = tid / SB) copies elements
+    //      e = t', t'+T, ... of system s0+q (coalesced over q) ----
+    {
+        const int q = threadIdx.x % SB;
+        const int tp = threadIdx.x / SB;
+        const int64_t s = s0 + q;
+        double *M = smem + q * per;
+        int bad = 0;
+        if (s < args.batch) {
+            if (LAYOUT == kInterleaved) {
+                int i = tp % n, j = tp / n;
+                for (int e = tp; e < nn; e += T) {
+                    const double v = ld_stream(Ag + static_cast<int64_t>(e) * args.ld + s);
+                    bad |= dev::is_nonfinite(v);
+                    M[i * RS + j] = v;
+                    i += T;
+                    while (i >= n) { i -= n; ++j; }
+                }
+                if (MODE == kGesv)
+                    for (int i2 = tp; i2 < n; i2 += T) M[i2 * RS + n] = ld_stream(args.b + static_cast<int64_t>(i2) * args.ld + s);
+            } else {
+                const double *src = Ag + s * nn;
+                int i = tp % n, j = tp / n;
+                for (int e = tp; e < nn; e += T) {
+                    const double v = ld_stream(src + e);
+                    bad |= dev::is_nonfinite(v);
+                    M[i * RS + j] = v;
+                    i += T;
+                    while (i >= n) { i -= n; ++j; }
+                }
+                if (MODE == kGesv)
+                    for (int i2 = tp; i2 < n; i2 += T) M[i2 * RS + n] = ld_stream(args.b + s * n + i2);
+            }
+        }
+        s_bad[threadIdx.x] = bad;
+    }
+    __syncthreads();
+
+    // ---- compute: lanes t = lane % T of a group own system q ----
+    const int lane = threadIdx.x & 31;
+    const int t = lane % T;
+    const int q = threadIdx.x / T;
+    const int64_t s = s0 + q;
+    const bool active = s < args.batch;
+    double *M = smem + q * per;
+    const int *piv = reinterpret_cast<const int *>(M + n * RS + 32);  // pivots (after 32 reciprocals)
+    // non-finite entries anywhere in this system (loaded by threads q + SB*t')
+    int badv = 0;
+    for (int tp = t; tp < T; tp += T) badv |= s_bad[q + SB * tp];
+    const bool bad = group_any_int<T>(badv) != 0;
+
+    const int info0 = smem_lupp<T, MODE == kGesv>(M, n, RS, t, args.tile, args.threshold);
+    int info = info0;
     if (bad) info = -1;
 
     // a7: store
@@ -274,6 +293,77 @@ __global__ void __launch_bounds__(128) k_smem_group(SolveArgs args, int n)
                 }
             }
         }
+    }
+}
+
+// Ragged batches (tl_lupp_solve_batched): persistent over the bucket of
+// systems of size n (run-time), SB = blockDim/T systems per block and trip;
+// each system at its own offsets in per-system column-major storage.  Same
+// elimination as k_smem_group (smem_lupp), binary64.
+template <int T>
+__global__ void __launch_bounds__(128) k_smem_ragged(RaggedArgs r, int n)
+{
+    extern __shared__ double smem[];
+    __shared__ int s_bad[128];
+    const int SB = blockDim.x / T;
+    const int per = smem_sys_doubles(n, T);
+    const int RS = smem_row_stride(n);
+    const int nn = n * n;
+    const int64_t beg = r.offsets[n];
+    const int64_t full = r.offsets[n + 1] - beg;
+    int64_t count = full;
+    if (r.counts) {
+        const int64_t c = r.counts[n];
+        count = c < 0 ? 0 : (c < full ? c : full);
+    }
+    const int lane = threadIdx.x & 31;
+    const int t = lane % T;
+    const int q = threadIdx.x / T;
+    for (int64_t base = static_cast<int64_t>(blockIdx.x) * SB; base < count;
+         base += static_cast<int64_t>(gridDim.x) * SB) {           // block-uniform trip
+        // load: thread (qL = tid % SB, tp = tid / SB) copies elements
+        // e = tp, tp+T, ... of system base+qL
+        {
+            const int qL = threadIdx.x % SB;
+            const int tp = threadIdx.x / SB;
+            double *M = smem + qL * per;
+            int bad = 0;
+            if (base + qL < count) {
+                const int64_t sidx = r.bucket[beg + base + qL];
+                const double *A = r.A + r.a_off[sidx];
+                int i = tp % n, j = tp / n;
+                for (int e = tp; e < nn; e += T) {
+                    const double v = ld_stream(A + e);
+                    bad |= dev::is_nonfinite(v);
+                    M[i * RS + j] = v;
+                    i += T;
+                    while (i >= n) { i -= n; ++j; }
+                }
+                const double *bv = r.b + r.b_off[sidx];
+                for (int i2 = tp; i2 < n; i2 += T) M[i2 * RS + n] = ld_stream(bv + i2);
+            }
+            s_bad[threadIdx.x] = bad;
+        }
+        __syncthreads();
+        const bool active = base + q < count;
+        double *M = smem + q * per;
+        int badv = 0;
+        for (int tp = t; tp < T; tp += T) badv |= s_bad[q + SB * tp];
+        const bool bad = group_any_int<T>(badv) != 0;
+        int info = smem_lupp<T, true>(M, n, RS, t, 0, 0.0);
+        if (bad) info = -1;
+        if (active) {
+            const int64_t sidx = r.bucket[beg + base + q];
+            const int *piv = reinterpret_cast<const int *>(M + n * RS + 32);
+            double *x = r.x + r.b_off[sidx];
+            int32_t *ip = r.ipiv + r.piv_off[sidx];
+            for (int i = t; i < n; i += T) {
+                st_stream(x + i, info != 0 ? dev::nan_value() : M[i * RS + n]);
+                st_stream(ip + i, bad ? i + 1 : piv[i] + 1);
+            }
+            if (t == 0) st_stream(r.info + sidx, info);
+        }
+        __syncthreads();  // the next trip's loads overwrite the blocks
     }
 }
 
