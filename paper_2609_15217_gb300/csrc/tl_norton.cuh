@@ -19,6 +19,7 @@ struct NortonParams {
 //   seq  = sqrt(3/2 s:s), n = 3/2 s / seq,
 //   F_el = de - deps + dp n,  F_p = dp - dt A seq^m,
 //   dF_el/dde = I + dp (2 mu / seq)(3/2 K - n n^T),  dF_el/ddp = n,
+//   (assembled as one FMA per entry around its constant part),
 //   dF_p/dde  = -dt A m seq^(m-1) 2 mu n^T,          dF_p/ddp = 1.
 __device__ __forceinline__ void norton_eval(const NortonParams &P, const double (&sig0)[6],
                                             const double (&deps)[6], const double (&x)[7],
@@ -50,13 +51,21 @@ __device__ __forceinline__ void norton_eval(const NortonParams &P, const double 
     for (int i = 0; i < 6; ++i) F[i] = fma(dp, n[i], x[i] - deps[i]);
     F[6] = dp - P.dt * P.Acoef * pw_m;
 
+    // dF_el/dde = I + c (3/2 K - n n^T) = C_ij - (c n_i) n_j with the
+    // constant part C_ij = delta_ij + 3/2 c K_ij: 1 + c on the normal
+    // diagonal, -c/2 between normal components, 1 + 3/2 c on the shear
+    // diagonal, 0 elsewhere; one FMA per entry
     const double c = dp * two_mu * inv;
+    const double c_nn = 1.0 + c, c_no = -0.5 * c, c_ss = fma(1.5, c, 1.0);
+    double cn[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) cn[i] = c * n[i];
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
-            const double kij = (i == j ? 1.0 : 0.0) - ((i < 3 && j < 3) ? 1.0 / 3.0 : 0.0);
-            J[i][j] = (i == j ? 1.0 : 0.0) + c * fma(1.5, kij, -n[i] * n[j]);
+            const double cij = (i < 3 && j < 3) ? (i == j ? c_nn : c_no) : (i == j ? c_ss : 0.0);
+            J[i][j] = fma(-cn[i], n[j], cij);
         }
 #pragma unroll
     for (int i = 0; i < 6; ++i) J[i][6] = n[i];
