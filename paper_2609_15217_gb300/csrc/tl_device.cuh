@@ -40,11 +40,6 @@
 #ifndef TL_GROUP_RCP_INT
 #define TL_GROUP_RCP_INT 0
 #endif
-// Group solvers: consume the broadcast pivot row column by column (1)
-// instead of keeping a copy of it in registers (0).
-#ifndef TL_GROUP_STREAM_U
-#define TL_GROUP_STREAM_U 0
-#endif
 
 namespace tl {
 namespace dev {
@@ -560,140 +555,6 @@ __device__ __forceinline__ void group_argmax(double &v, int &row)
     }
 }
 
-// Streamed-broadcast variant of lu_group_factor (same arithmetic, same
-// operation order per element): the pivot-row element u_kj arrives by the
-// interchange shuffle of column j and is consumed right away by that
-// column's updates, so no copy of the pivot row is kept in registers.
-template <int N, int T, bool KEEP_L, int NB>
-__device__ __forceinline__ int lu_group_factor_stream(double (&a)[Group<N, T>::K][N],
-                                                      double (&b)[Group<N, T>::K],
-                                                      int (&pivk)[Group<N, T>::K],
-                                                      double (&rcp)[Group<N, T>::K], int t, int lane0,
-                                                      bool &tiny)
-{
-    constexpr int K = Group<N, T>::K;
-    int info = 0;
-    auto search = [&](int k, double &cv, int &crow) {
-        cv = 0.0;
-        crow = N;
-#pragma unroll
-        for (int s = 0; s < K; ++s) {
-            if (s * T < N && (T - 1) + s * T >= k) {
-                const int i = t + s * T;
-                const bool cand = (i >= k) && (i < N);
-                const unsigned long long m = mag_bits(a[s][k]);
-                const bool take = cand && (crow == N || m > mag_bits(cv));
-                cv = sel(take, a[s][k], cv);
-                crow = take ? i : crow;
-            }
-        }
-        group_argmax<T>(cv, crow);
-    };
-    auto group_rcp = [](double v) {
-#if TL_GROUP_RCP_INT
-        return rcp_rn(v);
-#else
-        return __drcp_rn(v);
-#endif
-    };
-    // interchange of rows k and p in column j (j == N: the right-hand side);
-    // returns the new entry of row k (the pivot row's u_kj) on every lane
-    auto swap_col = [&](int j, int owner_k, int slot_k, int owner_p, int slot_p) -> double {
-        double vk, vp = 0.0;
-        if (j < N) {
-            vk = a[slot_k][j];
-#pragma unroll
-            for (int s = 0; s < K; ++s) vp = sel(s == slot_p, a[s][j], vp);
-        } else {
-            vk = b[slot_k];
-#pragma unroll
-            for (int s = 0; s < K; ++s) vp = sel(s == slot_p, b[s], vp);
-        }
-        const double new_k = __shfl_sync(0xffffffffu, vp, lane0 + owner_p);
-        const double new_p = __shfl_sync(0xffffffffu, vk, lane0 + owner_k);
-        if (j < N) {
-#pragma unroll
-            for (int s = 0; s < K; ++s) a[s][j] = sel(t == owner_p && s == slot_p, new_p, a[s][j]);
-            if (t == owner_k) a[slot_k][j] = new_k;
-        } else {
-#pragma unroll
-            for (int s = 0; s < K; ++s) b[s] = sel(t == owner_p && s == slot_p, new_p, b[s]);
-            if (t == owner_k) b[slot_k] = new_k;
-        }
-        return new_k;
-    };
-    double cv_next;
-    int crow_next;
-    search(0, cv_next, crow_next);
-    double r_next = group_rcp(cv_next);
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-        const int owner_k = k % T;
-        const int slot_k = k / T;
-        const double cv = cv_next;
-        const int p = crow_next;
-        const double r = r_next;
-        const bool zero = (mag_bits(cv) == 0ULL);
-        if (t == owner_k) pivk[slot_k] = p;
-        if (zero && info == 0) info = k + 1;
-        const int owner_p = p % T;
-        const int slot_p = p / T;
-        // a3 for the L part (getrf output) and column k
-#pragma unroll
-        for (int j = (KEEP_L ? 0 : k); j <= k; ++j) swap_col(j, owner_k, slot_k, owner_p, slot_p);
-        // a4: multipliers, kept negated
-        const bool small = !zero && mag_bits(cv) < kDblMinBits;
-        if (t == owner_k) rcp[slot_k] = r;
-        tiny = tiny || small;
-        const double nr = neg(r);
-#pragma unroll
-        for (int s = 0; s < K; ++s) {
-            if (Group<N, T>::slot_alive(s, k)) {
-                const int i = t + s * T;
-                if (zero && i > k && i < N) a[s][k] = neg(a[s][k]);
-            }
-        }
-        if (!__any_sync(0xffffffffu, small)) {
-#pragma unroll
-            for (int s = 0; s < K; ++s) {
-                if (Group<N, T>::slot_alive(s, k)) {
-                    const int i = t + s * T;
-                    if (!zero && i > k && i < N) a[s][k] = __dmul_rn(a[s][k], nr);
-                }
-            }
-        } else {
-            const double ncv = neg(cv);
-#pragma unroll
-            for (int s = 0; s < K; ++s) {
-                if (Group<N, T>::slot_alive(s, k)) {
-                    const int i = t + s * T;
-                    if (!zero && i > k && i < N) a[s][k] = small ? __ddiv_rn(a[s][k], ncv) : __dmul_rn(a[s][k], nr);
-                }
-            }
-        }
-        // a5, column k+1 first (look-ahead), then the others and b
-#pragma unroll
-        for (int j = k + 1; j < N + NB; ++j) {
-            const double u = swap_col(j, owner_k, slot_k, owner_p, slot_p);
-#pragma unroll
-            for (int s = 0; s < K; ++s) {
-                if (Group<N, T>::slot_alive(s, k)) {
-                    const int i = t + s * T;
-                    if (!zero && i > k && i < N) {
-                        if (j < N) a[s][j] = __fma_rn(a[s][k], u, a[s][j]);
-                        else b[s] = __fma_rn(a[s][k], u, b[s]);
-                    }
-                }
-            }
-            if (j == k + 1 && k + 1 < N) {
-                search(k + 1, cv_next, crow_next);
-                r_next = group_rcp(cv_next);
-            }
-        }
-    }
-    return info;
-}
-
 // Group LUpp.  Lane t (0..T-1) of the group holds rows t + s*T in a[s][*]
 // and, for NB = 1, the matching entries of the right-hand side in b[s].
 // `lane0` is the warp lane of the group's first lane.  `active` is false for
@@ -710,9 +571,6 @@ __device__ __forceinline__ int lu_group_factor(double (&a)[Group<N, T>::K][N],
                                                double (&rcp)[Group<N, T>::K], int t, int lane0,
                                                bool &tiny)
 {
-#if TL_GROUP_STREAM_U
-    return lu_group_factor_stream<N, T, KEEP_L, NB>(a, b, pivk, rcp, t, lane0, tiny);
-#endif
     constexpr int K = Group<N, T>::K;
     int info = 0;
     // a2: this lane's candidate in column k, then the butterfly across the
