@@ -57,6 +57,8 @@ tl_status newton_launch(tl_handle *h, int law_id, int n, const NewtonBatch &B, c
     if (law_id == TL_LAW_NORTON) return launch_persistent(h, reinterpret_cast<const void *>(&k_newton_norton), 1, B, stream);
     if (law_id != TL_LAW_TANH || n < 1 || n > TL_MAX_N) return TL_ERR_UNSUPPORTED;
     if (n <= kTanhThreadMaxN) return launch_persistent(h, tanh_thread_kernel(n), 1, B, stream);
+    tl_status st = TL_OK;
+    if (newton_tanh_smem_launch(h, n, B, stream, &st)) return st;
     const VariantList &l = registry(n, kPerSystem, kOpNewtonTanh);
     if (l.count == 0) return TL_ERR_UNSUPPORTED;
     return launch_persistent(h, l.v[0].kernel, l.v[0].lanes, B, stream);

@@ -36,6 +36,9 @@ struct NewtonBatch {
 
 // Launch the fused Newton kernel of a law (law_id, n) over B on stream.
 tl_status newton_launch(tl_handle *h, int law_id, int n, const NewtonBatch &B, cudaStream_t stream);
+// Shared-memory tanh-law kernel for 25 <= n <= 32: launches it and returns
+// true with *out set, or returns false for other n.
+bool newton_tanh_smem_launch(tl_handle *h, int n, const NewtonBatch &B, cudaStream_t stream, tl_status *out);
 // Law parameters of a descriptor into a job (false: invalid descriptor).
 bool law_params(const tl_law &law, NewtonJob *jb);
 
