@@ -325,14 +325,19 @@ tl_status tl_autotune(tl_handle *h, int n_min, int n_max, tl_layout layout,
  * table that tl_autotune fills (the size-aware "best X" dispatcher of
  * Sec. 4.1).
  *   variant  lanes + 100 * storage: lanes per system (1 = one thread per
- *            system, 2, 4, 8, 16), storage 0 = registers (a kernel compiled
- *            for that n), 1 = shared memory (run-time n, n >= 2).  0 restores
- *            the built-in default.  A variant not built for n is rejected
- *            with TL_ERR_INVALID_ARG (argument 4).
+ *            system, 2, 4, 8, 16, 32), storage 0 = registers (a kernel
+ *            compiled for that n; 1..16 lanes), 1 = shared memory (run-time
+ *            n, n >= 2; 2..32 lanes).  0 restores the built-in default.  A
+ *            variant not built for n is rejected with TL_ERR_INVALID_ARG
+ *            (argument 4).
  *   block    0 (occupancy + wave-fill heuristic) or 32, 64, 128 threads.
  * The choice applies to tl_gesv_batched and tl_getrf_batched for (n,
- * layout); tl_getrs_batched and tl_lupp_solve_batched use the register
- * kernel with the same lane count when one exists.
+ * layout); tl_getrs_batched and the mixed-precision part of
+ * tl_lupp_solve_batched use the register kernel with the same lane count
+ * when one exists, the binary64 part of tl_lupp_solve_batched the register
+ * or shared-memory ragged kernel of the same id when one exists (its
+ * default: register kernels up to n = 16, shared memory with 16 lanes up to
+ * n = 26, 32 lanes above).
  */
 tl_status tl_dispatch_set(tl_handle *h, int n, tl_layout layout, int variant, int block);
 tl_status tl_dispatch_get(tl_handle *h, int n, tl_layout layout, int *variant, int *block);
