@@ -653,6 +653,17 @@ def oracle_sweep_rate(n_list, target_s=0.3, samples=None, seed_base=1236, max_sa
     return total_S / total_t, threads, sample
 
 
+def sweep_config(n_list, world, systems=None):
+    """The `config` object of the contract line (both arms)."""
+    return {"workload": "standalone FP64 sweep: n=1..32, 2^20 systems per n capped at 6 GiB "
+                        "(n>=27), half U[-1,1], half kappa in [1e2,1e8], b=A x_true; interleaved "
+                        "batch-minor layout, tl_gesv_batched",
+            "systems_per_step": systems if systems is not None else sum(sweep_batch(n) for n in n_list),
+            "L2": "inputs larger than L2 (each step streams "
+                  f"{sum(bytes_per_system(n) * sweep_batch(n) for n in n_list) / 1e9:.1f} GB)",
+            "parallelism": f"replicas x{world}"}
+
+
 def reference_arm(args):
     """--impl reference: the CPU oracle (as it stands) on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -672,10 +683,10 @@ def reference_arm(args):
                    + "), time extrapolated linearly to the full per-n batch sizes")
     out = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sum(sweep_batch(n) for n in n_list) / v * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "standalone FP64 sweep n=1..32, 2^20 systems per n (6 GiB cap), interleaved",
-                   "L2": "n/a (host)"},
+        "config": sweep_config(n_list, 1),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample_desc},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": time.perf_counter() - t_all,
@@ -863,12 +874,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": med_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "standalone FP64 sweep: n=1..32, 2^20 systems per n capped at 6 GiB "
-                                   "(n>=27), half U[-1,1], half kappa in [1e2,1e8], b=A x_true; interleaved "
-                                   "batch-minor layout, tl_gesv_batched",
-                       "systems_per_step": systems_rank, "L2": "inputs larger than L2 (each step streams "
-                       f"{sum(bytes_per_system(n) * sweep_batch(n) for n in n_list) / 1e9:.1f} GB)",
-                       "parallelism": f"replicas x{world}"},
+            "config": sweep_config(n_list, world, systems_rank),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "per_n": per_n_out, "gen_s": gen_s, "dispatch": tune, **extra,
         }
