@@ -31,10 +31,15 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-// Reciprocal of the one-thread fast path: the FP64 instruction (0) or the
-// integer-pipe sequence (1).
-#ifndef TL_THREAD_RCP_INT
-#define TL_THREAD_RCP_INT 0
+// Reciprocal of the one-thread fast path of the batched solvers: the
+// integer-pipe sequence up to this n, the FP64 instruction above it.
+// Measured on GB300: the integer sequence wins for n <= 5 (0.64-0.72 of the
+// FP64 peak at n = 4, 5 against 0.47-0.56) and loses for n = 6..9, where
+// its registers cost more than the FP64 slots it saves.  The Newton kernels,
+// whose FP64 pipe is saturated by the law, always take the integer
+// sequence (+10% points/s).
+#ifndef TL_THREAD_RCP_INT_MAX_N
+#define TL_THREAD_RCP_INT_MAX_N 5
 #endif
 // Reciprocal of the sub-warp group solvers (same choice).
 #ifndef TL_GROUP_RCP_INT
@@ -331,7 +336,7 @@ __device__ __forceinline__ int lu_thread_factor(double (&a)[N][N], double (&b)[N
 // Returns true when the system needs the exact general path instead (a zero,
 // subnormal, huge or non-finite pivot was met): the caller then restarts the
 // system from its input with lu_thread_factor.
-template <int N, bool KEEP_L, int NB>
+template <int N, bool KEEP_L, int NB, bool RCP_INT = (N <= TL_THREAD_RCP_INT_MAX_N)>
 __device__ __forceinline__ bool lu_thread_factor_fast(double (&a)[N][N], double (&b)[NB > 0 ? NB : 1][N],
                                                       int (&piv)[N], double (&rcp)[N])
 {
@@ -356,11 +361,7 @@ __device__ __forceinline__ bool lu_thread_factor_fast(double (&a)[N][N], double 
         }
         slow = slow || !rcp_fast_ok(best);
         piv[k] = p;
-#if TL_THREAD_RCP_INT
-        const double r = rcp_rn_fast(pv);
-#else
-        const double r = __drcp_rn(pv);
-#endif
+        const double r = RCP_INT ? rcp_rn_fast(pv) : __drcp_rn(pv);
         rcp[k] = r;
         // a3: interchange as a register permutation
         const int j0 = KEEP_L ? 0 : k;
@@ -511,13 +512,13 @@ __device__ __forceinline__ int lupp_solve(double (&a)[N][N], double (&b)[N], int
 // The fast solve: returns false when it cannot vouch for the result (the
 // system met a zero, tiny, huge or non-finite pivot or input); the caller must
 // then restore a and b and use lupp_solve.  Same arithmetic otherwise.
-template <int N>
+template <int N, bool RCP_INT = (N <= TL_THREAD_RCP_INT_MAX_N)>
 __device__ __forceinline__ bool lupp_solve_fast(double (&a)[N][N], double (&b)[N], int (&piv)[N])
 {
     const bool bad = any_nonfinite<N>(a);
     double rcp[N];
     double (&bb)[1][N] = *reinterpret_cast<double (*)[1][N]>(&b);
-    const bool slow = lu_thread_factor_fast<N, false, 1>(a, bb, piv, rcp);
+    const bool slow = lu_thread_factor_fast<N, false, 1, RCP_INT>(a, bb, piv, rcp);
     lu_thread_backsolve_fast<N>(a, b, rcp);
     return !(slow || bad);
 }

@@ -154,7 +154,7 @@ static __global__ void __launch_bounds__(128) k_newton_norton(NewtonBatch B)
             for (int i = 0; i < 7; ++i) rhs[i] = dev::neg(F[i]);
             int piv[7];
             int info = 0;
-            if (!dev::lupp_solve_fast<7>(J, rhs, piv)) {
+            if (!dev::lupp_solve_fast<7, true>(J, rhs, piv)) {
                 NortonState ns;
 #pragma unroll
                 for (int i = 0; i < 6; ++i) {
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(128) k_newton_tanh(NewtonBatch B)
             for (int i = 0; i < N; ++i) rhs[i] = dev::neg(F[i]);
             int piv[N];
             int info = 0;
-            if (!dev::lupp_solve_fast<N>(J, rhs, piv)) {
+            if (!dev::lupp_solve_fast<N, true>(J, rhs, piv)) {
                 VecN<N> xv;
 #pragma unroll
                 for (int i = 0; i < N; ++i) xv.v[i] = x[i];
