@@ -64,7 +64,7 @@ typedef enum {
     TL_ERR_INVALID_ARG = -1,   /* see tl_last_bad_arg()                     */
     TL_ERR_CUDA = -2,          /* see tl_last_cuda_error()                  */
     TL_ERR_NO_MEMORY = -3,     /* workspace could not be allocated          */
-    TL_ERR_UNSUPPORTED = -4,   /* valid request this build does not serve   */
+    TL_ERR_UNSUPPORTED = -4,   /* valid request the library does not support */
     TL_ERR_TIMEOUT = -5        /* a bounded device wait gave up             */
 } tl_status;
 

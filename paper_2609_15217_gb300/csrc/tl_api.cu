@@ -244,7 +244,7 @@ const char *tl_status_string(tl_status s)
     case TL_ERR_INVALID_ARG: return "TL_ERR_INVALID_ARG: an argument was rejected (see tl_last_bad_arg)";
     case TL_ERR_CUDA: return "TL_ERR_CUDA: a CUDA call failed (see tl_last_cuda_error)";
     case TL_ERR_NO_MEMORY: return "TL_ERR_NO_MEMORY: workspace allocation failed";
-    case TL_ERR_UNSUPPORTED: return "TL_ERR_UNSUPPORTED: request not served by this build";
+    case TL_ERR_UNSUPPORTED: return "TL_ERR_UNSUPPORTED: request not supported by the library";
     case TL_ERR_TIMEOUT: return "TL_ERR_TIMEOUT: a bounded device wait gave up";
     }
     return "unknown tl_status";
