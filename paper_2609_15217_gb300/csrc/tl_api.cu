@@ -47,12 +47,11 @@ int default_register_lanes(int n)
 }
 
 // Lanes per system of the mixed-precision ragged kernel before any tuning.
-int default_ir_lanes(int n)
+int default_ir_id(int n)
 {
-    if (n <= 10) return 1;
-    if (n <= 16) return 4;
-    if (n <= 24) return 8;
-    return 16;
+    if (n <= 10) return variant_id(1, 0);
+    if (n <= 16) return variant_id(4, 0);
+    return variant_id(32, 1);
 }
 
 int default_ragged_id(int n)

@@ -63,12 +63,12 @@ extern "C" tl_status tl_dispatch_set(tl_handle *h, int n, tl_layout layout, int 
         const VariantList &lo = registry(n, layout, op);
         for (int i = 0; i < lo.count; ++i)
             if (lo.v[i].kind == 0 && lo.v[i].lanes == lanes) h->choice[n][layout][op] = Choice{lanes, 0};
-        // the ragged solve also has shared-memory kernels (per-system slot)
-        if (op == kOpRagged && variant >= 100) {
-            const VariantList &lr = registry(n, kPerSystem, kOpRagged);
+        // the ragged solves also have shared-memory kernels (per-system slot)
+        if ((op == kOpRagged || op == kOpRaggedIr) && variant >= 100) {
+            const VariantList &lr = registry(n, kPerSystem, op);
             for (int i = 0; i < lr.count; ++i)
                 if (variant_id(lr.v[i].lanes, lr.v[i].kind) == variant)
-                    h->choice[n][kPerSystem][kOpRagged] = Choice{variant, 0};
+                    h->choice[n][kPerSystem][op] = Choice{variant, 0};
         }
     }
     return TL_OK;

@@ -125,14 +125,14 @@ unsigned ragged_grid(tl_handle *h, const Variant *v, int64_t batch, int blk)
     return static_cast<unsigned>(need < resident ? need : resident);
 }
 
-// Persistent launch of a shared-memory ragged kernel for size nn.
+// Persistent launch of a shared-memory ragged kernel for size nn with `per`
+// bytes of shared memory per system.
 tl_status launch_smem_ragged(tl_handle *h, const Variant *v, int nn, int64_t batch, RaggedArgs &r,
-                             cudaStream_t stream)
+                             cudaStream_t stream, size_t per)
 {
     int limit = 0;
     tl_status st = smem_opt_in(h, v->kernel, &limit);
     if (st != TL_OK) return st;
-    const size_t per = smem_sys_bytes(nn, v->lanes);
     for (int blk : {128, 64, 32}) {
         if (blk < v->lanes) continue;
         const size_t smem = static_cast<size_t>(blk / v->lanes) * per;
@@ -160,7 +160,7 @@ tl_status launch_binary64(tl_handle *h, int64_t batch, RaggedArgs &r, cudaStream
         const Variant *v = find_variant(nn, kPerSystem, kOpRagged, c.lanes ? c.lanes : default_ragged_id(nn));
         if (!v) return TL_ERR_UNSUPPORTED;
         if (v->kind == 1) {
-            const tl_status st = launch_smem_ragged(h, v, nn, batch, r, stream);
+            const tl_status st = launch_smem_ragged(h, v, nn, batch, r, stream, smem_sys_bytes(nn, v->lanes));
             if (st != TL_OK) return st;
             continue;
         }
@@ -207,8 +207,13 @@ tl_status ragged_solve(tl_handle *h, int64_t batch, const int32_t *n, RaggedArgs
     for (int nn = 1; nn <= TL_MAX_N; ++nn) {
         const Choice &c = h->choice[nn][kPerSystem][kOpRaggedIr];
         const Variant *v =
-            find_variant(nn, kPerSystem, kOpRaggedIr, c.lanes ? c.lanes : variant_id(default_ir_lanes(nn), 0));
+            find_variant(nn, kPerSystem, kOpRaggedIr, c.lanes ? c.lanes : default_ir_id(nn));
         if (!v) return TL_ERR_UNSUPPORTED;
+        if (v->kind == 1) {
+            const tl_status st = launch_smem_ragged(h, v, nn, batch, r, stream, ir_smem_bytes_per_system(nn));
+            if (st != TL_OK) return st;
+            continue;
+        }
         const int blk = 128;
         const unsigned g = ragged_grid(h, v, batch, blk);
         void *params[] = {&r};

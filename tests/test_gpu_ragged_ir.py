@@ -138,3 +138,45 @@ def test_ir_repeated_calls_and_binary64_mode(tl, h):
         # TL_PREC_FP64 leaves refine_steps alone
         _, _, _, ref64 = run_ir(tl, h, sizes, a_off, b_off, p_off, Abuf, bbuf, npiv, prec=0)
         assert (ref64 == -9).all()
+
+
+def _special(systems, a_off, b_off, Abuf, bbuf, n):
+    """Plant the special systems of test_ir_special_systems at size n."""
+    idx, A, b = systems[n]
+    pos = {s: q for q, s in enumerate(idx)}
+    edits = {0: (1, 1, 1e39), 1: (n - 1, 0, 1e-39), 2: (0, n - 1, np.nan)}
+    for s, (i, j, v) in edits.items():
+        A[pos[s], i, j] = v
+    A[pos[3], :, n // 2] = 0.0
+    b[pos[4]] = 0.0
+    A[pos[5]] = np.eye(n) * 2.0
+    b[pos[5]] = np.arange(n, dtype=float)
+    for s in range(6):
+        q = pos[s]
+        Abuf[a_off[s]:a_off[s] + n * n] = A[q].T.reshape(-1)
+        bbuf[b_off[s]:b_off[s] + n] = b[q]
+
+
+IR_VARIANT_CASES = ([(n, 132) for n in (2, 3, 5, 9, 10, 11, 16, 17, 20, 24, 25, 28, 31, 32)]
+                    + [(n, 8) for n in (17, 20, 24)] + [(n, 16) for n in (25, 28, 32)])
+
+
+@pytest.mark.parametrize("n,variant", IR_VARIANT_CASES)
+def test_ir_each_kernel_with_special_systems(tl, h, n, variant):
+    """Every mixed-precision kernel (the shared-memory warp kernel at every
+    kind of n, the register group kernels at the sizes where they are not the
+    default) on one size, with the special systems planted in the batch and
+    a batch that is not a multiple of the warps per block."""
+    sizes = np.full(333, n, np.int64)
+    systems, a_off, b_off, p_off, Abuf, bbuf, npiv = make_ragged(sizes, 400 + n)
+    _special(systems, a_off, b_off, Abuf, bbuf, n)
+    assert tl.tl_dispatch_set(h, n, tl.TL_LAYOUT_PER_SYSTEM, variant, 0) == tl.TL_OK
+    try:
+        x, piv, info, ref = run_ir(tl, h, sizes, a_off, b_off, p_off, Abuf, bbuf, npiv)
+    finally:
+        tl.tl_dispatch_set(h, n, tl.TL_LAYOUT_PER_SYSTEM, 0, 0)
+    stats = check_ir(systems, b_off, p_off, x, piv, info, ref)
+    assert (ref[:4] == -1).all() and info[2] == -1 and info[3] == n // 2 + 1
+    assert ref[4] == 0 and ref[5] == 0
+    assert np.array_equal(x[b_off[5]:b_off[5] + n], np.arange(n) / 2.0)
+    assert stats[n][0] >= 4 and sum(stats[n][1:]) > 200
