@@ -31,7 +31,6 @@ int default_register_lanes(int n);
 // Default mixed-precision ragged variant id for n: one thread, then 4 lanes
 // per system in registers, then the shared-memory warp kernel.
 int default_ir_id(int n);
-size_t ir_smem_bytes_per_system(int n);
 const Variant *find_variant(int n, int layout, int op, int id);
 tl_status fail_arg(tl_handle *h, int pos);
 tl_status fail_cuda(tl_handle *h, cudaError_t e);

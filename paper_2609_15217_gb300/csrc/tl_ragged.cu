@@ -11,6 +11,7 @@
 #include "tinylu.h"
 #include "tl_handle.h"
 #include "tl_internal.h"
+#include "tl_ir_smem.cuh"
 #include "tl_smem.cuh"
 
 namespace tl {
