@@ -332,12 +332,13 @@ tl_status tl_autotune(tl_handle *h, int n_min, int n_max, tl_layout layout,
  *            (argument 4).
  *   block    0 (occupancy + wave-fill heuristic) or 32, 64, 128 threads.
  * The choice applies to tl_gesv_batched and tl_getrf_batched for (n,
- * layout); tl_getrs_batched and the mixed-precision part of
- * tl_lupp_solve_batched use the register kernel with the same lane count
- * when one exists, the binary64 part of tl_lupp_solve_batched the register
- * or shared-memory ragged kernel of the same id when one exists (its
- * default: register kernels up to n = 16, shared memory with 16 lanes up to
- * n = 26, 32 lanes above).
+ * layout); tl_getrs_batched uses the register kernel with the same lane
+ * count when one exists; the two parts of tl_lupp_solve_batched take the
+ * register or shared-memory ragged kernel of the same id when one exists.
+ * Their defaults: binary64, register kernels up to n = 16, shared memory
+ * with 16 lanes up to n = 26, 32 lanes above; mixed precision, one thread
+ * per system up to n = 10, 4 lanes in registers up to n = 16, one warp per
+ * system in shared memory (id 132) above.
  */
 tl_status tl_dispatch_set(tl_handle *h, int n, tl_layout layout, int variant, int block);
 tl_status tl_dispatch_get(tl_handle *h, int n, tl_layout layout, int *variant, int *block);
