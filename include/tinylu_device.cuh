@@ -1,4 +1,7 @@
-// tl_device.cuh -- device-callable tiny LUpp solvers for sm_103a.
+// tinylu_device.cuh -- device-callable tiny LUpp solvers for sm_103a: the
+// public header for user kernels (the tl::lupp_solve* entry points at the
+// end of this file) and the code the library's batched and fused Newton
+// kernels are built on.  Self-contained: include it alone in a .cu file.
 //
 // Two thread-to-system mappings (paper Sec. 2.3, "thread-to-system mapping"):
 //
@@ -750,4 +753,81 @@ __device__ __forceinline__ void lu_group_backsolve(const double (&a)[Group<N, T>
 }
 
 }  // namespace dev
+}  // namespace tl
+
+// ===========================================================================
+// Public device-callable API: the LUpp solve of Sec. 2.2 called per system
+// from a user's own kernel (the device-callable form of Sec. 2.3, used the
+// same way inside the fused Newton loop of Algorithm 2).  Arithmetic: first
+// maximum of |a_ik| as pivot, l_ik = a_ik * RN(1/a_kk) (a quotient when
+// |a_kk| < DBL_MIN), one fma per update in increasing k, then
+// x_i = y_i * RN(1/u_ii); the pivots and info equal those of the textbook
+// elimination in this arithmetic bit for bit.
+// ===========================================================================
+namespace tl {
+
+// One system per calling thread, held in its registers (N <= 9 keeps the
+// matrix in registers without spilling).
+//   a     a[i][j] = A_ij on entry; destroyed.
+//   b     the right-hand side on entry, x on return (NaN when info != 0).
+//   ipiv  on return ipiv[k] = the 1-based row interchanged with row k at
+//         step k (LAPACK convention).
+// Returns info: 0; k + 1 when the pivot of step k is exactly zero (the first
+// such k; the factorization completes); -1 when A holds a NaN or an
+// infinity (nothing factored, ipiv the identity).
+template <int N>
+__device__ __forceinline__ int lupp_solve(double (&a)[N][N], double (&b)[N], int (&ipiv)[N])
+{
+    int piv[N];
+    const int info = dev::lupp_solve<N>(a, b, piv);
+#pragma unroll
+    for (int k = 0; k < N; ++k) ipiv[k] = piv[k] + 1;
+    return info;
+}
+
+// T consecutive lanes per system (T = 2, 4, 8, 16 or 32; the 32 / T groups
+// of a warp each solve their own system).  Lane t of a group holds the rows
+// t, t + T, t + 2T, ...: a[s][j] = A_{t+sT, j} and b[s] = b_{t+sT}; slots of
+// rows past N are ignored.  On return b[s] = x_{t+sT} (NaN when
+// info != 0) and ipiv[s] = the 1-based row interchanged at step t + sT.
+// Returns info (as lupp_solve) on every lane of the group.  Every lane of
+// the warp must call it together (the pivot search and the row interchanges
+// are shuffles); a group without a system of its own passes any finite
+// values and ignores the result.
+template <int N, int T>
+__device__ __forceinline__ int lupp_solve_subwarp(double (&a)[dev::Group<N, T>::K][N],
+                                                  double (&b)[dev::Group<N, T>::K],
+                                                  int (&ipiv)[dev::Group<N, T>::K])
+{
+    constexpr int K = dev::Group<N, T>::K;
+    const int lane = static_cast<int>(threadIdx.x) & 31;
+    const int t = lane % T;
+    const int lane0 = lane - t;
+    int bad = 0;
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+        const bool row = t + s * T < N;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            if (!row) a[s][j] = 0.0;
+            bad |= dev::is_nonfinite(a[s][j]) ? 1 : 0;
+        }
+        if (!row) b[s] = 0.0;
+    }
+#pragma unroll
+    for (int off = T / 2; off >= 1; off >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, off);
+    int pivk[K];
+    double rcp[K];
+    bool tiny = false;
+    int info = dev::lu_group_factor<N, T, false, 1>(a, b, pivk, rcp, t, lane0, tiny);
+    dev::lu_group_backsolve<N, T>(a, b, rcp, t, lane0, tiny);
+    if (bad) info = -1;
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+        ipiv[s] = (bad ? t + s * T : pivk[s]) + 1;
+        if (info != 0) b[s] = dev::nan_value();
+    }
+    return info;
+}
+
 }  // namespace tl

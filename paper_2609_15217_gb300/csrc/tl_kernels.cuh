@@ -1,8 +1,8 @@
 // tl_kernels.cuh -- batched LUpp kernels (gesv / getrf / getrs) built on the
-// device-callable solvers of tl_device.cuh, for the two storage layouts of
+// device-callable solvers of tinylu_device.cuh, for the two storage layouts of
 // the C ABI.  Instantiated per system size N in tl_inst_*.cu.
 #pragma once
-#include "tl_device.cuh"
+#include "tinylu_device.cuh"
 #include "tl_internal.h"
 
 namespace tl {

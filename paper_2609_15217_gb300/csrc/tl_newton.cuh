@@ -14,7 +14,7 @@
 //                          LUpp in registers;
 //   k_newton_tanh<N>       the same for the tanh law, N <= 9;
 //   k_newton_tanh_group<N,T>  T lanes per point (row-cyclic rows, the
-//                          sub-warp LUpp of tl_device.cuh), N >= 10.
+//                          sub-warp LUpp of tinylu_device.cuh), N >= 10.
 // All are persistent: when a point stops (converged, iteration cap,
 // singular, non-finite) its thread (group) stores the results and takes the
 // next point of its stride, so a lane idles for one solve per point instead
@@ -24,7 +24,7 @@
 #include <cmath>
 
 #include "tinylu.h"
-#include "tl_device.cuh"
+#include "tinylu_device.cuh"
 #include "tl_internal.h"
 #include "tl_kernels.cuh"
 #include "tl_newton_types.h"

@@ -12,7 +12,7 @@
 #include <cmath>
 
 #include "tinylu.h"
-#include "tl_device.cuh"
+#include "tinylu_device.cuh"
 #include "tl_handle.h"
 #include "tl_internal.h"
 #include "tl_norton.cuh"

@@ -15,7 +15,7 @@
 // the whole warp, so no FP64 instruction is issued for a dead column chunk.
 // Loops over rows run at run time, so the code stays small whatever n is.
 //
-// Arithmetic is the same as the register solvers of tl_device.cuh (negated
+// Arithmetic is the same as the register solvers of tinylu_device.cuh (negated
 // multipliers a_ik * (-RN(1/a_kk)), one FMA per update in increasing k, the
 // back substitution by RN(1/u_ii)); LU and pivots are bit-identical to the
 // sequential elimination.
