@@ -2,7 +2,7 @@
 // __drcp_rn on the same inputs (compiled by tests/test_gpu_reciprocal.py).
 #include <cstdint>
 
-#include "tl_device.cuh"
+#include "tinylu_device.cuh"
 
 __global__ void k_rcp_check(const double *in, double *ours, double *ref, int64_t n)
 {
