@@ -86,7 +86,7 @@ FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12
 # DRAM bytes per system measured by ncu for the current kernels, keyed by
 # (variant, n) (dram__bytes_read.sum + dram__bytes_write.sum of one launch /
 # systems); an entry must be removed whenever its kernel changes.
-DRAM_BYTES_PER_SYSTEM = {(132, 32): 8786}
+DRAM_BYTES_PER_SYSTEM = {}
 
 VARIANT_NAMES = {1: "k_factor_thread", 2: "k_factor_group<T=2>", 4: "k_factor_group<T=4>",
                  8: "k_factor_group<T=8>", 16: "k_factor_group<T=16>", 102: "k_smem_group<T=2>",

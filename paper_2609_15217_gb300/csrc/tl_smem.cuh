@@ -14,6 +14,10 @@
 // one row or column.  The column loop stops at a bound that is the same for
 // the whole warp, so no FP64 instruction is issued for a dead column chunk.
 // Loops over rows run at run time, so the code stays small whatever n is.
+// With 32 lanes (one warp per system) the trailing block is instead walked
+// element by element, row-major, lane t taking every 32nd element: the
+// tile's rounding of rows to 8 and columns to 4 costs up to a quarter of the
+// FP64 instructions there, the element walk none.
 //
 // Arithmetic is the same as the register solvers of tinylu_device.cuh (negated
 // multipliers a_ik * (-RN(1/a_kk)), one FMA per update in increasing k, the
@@ -153,7 +157,32 @@ __device__ __forceinline__ int smem_lupp(double *M, int n, int RS, int t, int ti
         // (the same count on every lane of the warp) and possibly one tail
         // column; the chunks are a straight-line fall-through block entered
         // once per row, with immediate offsets from the row pointer.
-        if (!zero) {
+        if (!zero && T == 32) {
+            // one warp per system: the R x C trailing block (R = n-k-1 rows,
+            // C live columns) is walked row-major, lane t taking the elements
+            // t, t+32, t+64, ...; every lane issues ceil(R C / 32) FMAs, the
+            // least any split can (the 8 x 4 lane tile issues
+            // ceil(R/8) ceil(C/4)).  l_i and u_j come from shared memory.
+            const int ncols = wcols - (k + 1);
+            const int nrows = n - (k + 1);
+            const int nel = nrows * ncols;
+            if (nel > 0) {
+                const int q = T / ncols, rq = T % ncols;  // (row, column) advance per stride
+                int ei = t / ncols, ej = t % ncols;        // element t: row k+1+ei, column k+1+ej
+                const double *urow = M + k * RS + k + 1;
+                for (int e = t; e < nel; e += T) {
+                    double *Mi = M + (k + 1 + ei) * RS;
+                    const double l = Mi[k];
+                    Mi[k + 1 + ej] = __fma_rn(l, urow[ej], Mi[k + 1 + ej]);
+                    ej += rq;
+                    ei += q;
+                    if (ej >= ncols) {
+                        ej -= ncols;
+                        ++ei;
+                    }
+                }
+            }
+        } else if (!zero) {
             const int ncols = wcols - (k + 1);
             const int nfull = ncols / TC;
             const bool has_tail = tc < ncols - nfull * TC;
