@@ -14,9 +14,9 @@
 // one row or column.  The column loop stops at a bound that is the same for
 // the whole warp, so no FP64 instruction is issued for a dead column chunk.
 // Loops over rows run at run time, so the code stays small whatever n is.
-// With 32 lanes (one warp per system) the trailing block is instead walked
-// element by element, row-major, lane t taking every 32nd element: the
-// tile's rounding of rows to 8 and columns to 4 costs up to a quarter of the
+// With 16 or 32 lanes per system the trailing block is instead walked
+// element by element, row-major, lane t taking every T-th element: the
+// tile's rounding of rows and columns to the tile shape costs 15-20% of the
 // FP64 instructions there, the element walk none.
 //
 // Arithmetic is the same as the register solvers of tinylu_device.cuh (negated
@@ -157,12 +157,12 @@ __device__ __forceinline__ int smem_lupp(double *M, int n, int RS, int t, int ti
         // (the same count on every lane of the warp) and possibly one tail
         // column; the chunks are a straight-line fall-through block entered
         // once per row, with immediate offsets from the row pointer.
-        if (!zero && T == 32) {
-            // one warp per system: the R x C trailing block (R = n-k-1 rows,
-            // C live columns) is walked row-major, lane t taking the elements
-            // t, t+32, t+64, ...; every lane issues ceil(R C / 32) FMAs, the
-            // least any split can (the 8 x 4 lane tile issues
-            // ceil(R/8) ceil(C/4)).  l_i and u_j come from shared memory.
+        if (!zero && T >= 16) {
+            // 16 or 32 lanes per system: the R x C trailing block (R = n-k-1
+            // rows, C live columns) is walked row-major, lane t taking the
+            // elements t, t+T, t+2T, ...; every lane issues ceil(R C / T)
+            // FMAs, the least any split can (a TR x TC lane tile issues
+            // ceil(R/TR) ceil(C/TC)).  l_i and u_j come from shared memory.
             const int ncols = wcols - (k + 1);
             const int nrows = n - (k + 1);
             const int nel = nrows * ncols;
