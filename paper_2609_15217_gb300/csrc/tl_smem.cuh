@@ -153,10 +153,6 @@ __device__ __forceinline__ int smem_lupp(double *M, int n, int RS, int t, int ti
         }
         __syncwarp();
         // a5 (+ forward part of a6 through column n): a_ij += (-l_ik) u_kj.
-        // Lane (tr, tc) owns columns k+1+tc + c*TC: nfull whole chunks
-        // (the same count on every lane of the warp) and possibly one tail
-        // column; the chunks are a straight-line fall-through block entered
-        // once per row, with immediate offsets from the row pointer.
         if (!zero && T >= 16) {
             // 16 or 32 lanes per system: the R x C trailing block (R = n-k-1
             // rows, C live columns) is walked row-major, lane t taking the
@@ -183,6 +179,11 @@ __device__ __forceinline__ int smem_lupp(double *M, int n, int RS, int t, int ti
                 }
             }
         } else if (!zero) {
+            // fewer lanes: lane (tr, tc) owns columns k+1+tc + c*TC: nfull
+            // whole chunks (the same count on every lane of the warp) and
+            // possibly one tail column; the chunks are a straight-line
+            // fall-through block entered once per row, with immediate
+            // offsets from the row pointer
             const int ncols = wcols - (k + 1);
             const int nfull = ncols / TC;
             const bool has_tail = tc < ncols - nfull * TC;
