@@ -7,8 +7,8 @@
 // T lanes sharing the columns.
 //
 // Work split: at elimination step k the m = n-k-1 live rows and the n-k live
-// columns (b included) are cut among a TR x TC tile of lanes (4 x 4 for
-// T = 16): lane (tr, tc) keeps its columns of the pivot row in registers and
+// columns (b included) are cut among a TR x TC tile of lanes (2 x 4 for
+// T = 8): lane (tr, tc) keeps its columns of the pivot row in registers and
 // walks its rows, one multiplier per row, so an update costs one shared
 // load and one store; every lane has the same number of live elements up to
 // one row or column.  The column loop stops at a bound that is the same for
@@ -27,12 +27,8 @@
 #include "tinylu.h"
 #include "tl_kernels.cuh"
 
-// Columns per lane tile row for 32 lanes per system (tile 8 x 4 or 4 x 8:
-// measured equal on GB300), and the unroll factor of the row loop of the
-// trailing update (2 measured 5-10% slower than 1).
-#ifndef TL_SMEM_TC32
-#define TL_SMEM_TC32 4
-#endif
+// Unroll factor of the row loop of the lane-tile trailing update (2
+// measured 5-10% slower than 1).
 #ifndef TL_SMEM_ROW_UNROLL
 #define TL_SMEM_ROW_UNROLL 1
 #endif
@@ -86,7 +82,7 @@ template <int T, bool SOLVE>
 __device__ __forceinline__ int smem_lupp(double *M, int n, int RS, int t, int tile, double threshold)
 {
     constexpr int MODE = SOLVE ? kGesv : kGetrf;
-    constexpr int TC = (T == 32) ? TL_SMEM_TC32 : (T >= 4) ? 4 : T;
+    constexpr int TC = (T >= 4) ? 4 : T;  // lane tile (T <= 8; 16 and 32 lanes walk elements)
     constexpr int TR = T / TC;
     constexpr int MAXC = TL_MAX_N / TC;  // whole column chunks per lane (at most 32 live columns)
     static_assert(MAXC <= 16, "the chunk switch below covers 16 chunks");
