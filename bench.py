@@ -808,7 +808,8 @@ def main():
                 "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": traffic * data[dom]["S"] if traffic else None,
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per system on a smaller batch "
-                                  "of the same kernel and n, scaled to the launch" if traffic else None,
+                                  "of the same kernel and n, scaled to the launch" if traffic else
+                                  "null: no ncu DRAM counters taken on the current version of this kernel",
                 "peak_source": "derived: 152 SMs x 4 SMSPs x 0.5 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25)",
                 "kernel_share_of_step": fam_ms[fam] / sum(fam_ms.values()),
                 "kernel_n": fam_n,
