@@ -77,10 +77,12 @@ def bytes_per_system(n):
     return 8 * n * n + 8 * n + 8 * n + 4 * n + 4
 
 
-# FP64 pipe of the GB300: 152 SMs x 4 sub-partitions x 0.5 DFMA lane/clock
-# (measured: one warp-wide DFMA per 64 clocks per sub-partition) x 2 flops x
-# 2.07 GHz maximum SM clock.
-FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12
+# FP64 pipe of the GB300 from its unit counts: 152 SMs x 4 sub-partitions x
+# 0.5 DFMA lane/clock (one warp-wide DFMA per 64 clocks per sub-partition) x
+# 2 flops x 2.07 GHz maximum SM clock.  The roofline denominator is the rate
+# tl_measure_fma_peak measures in the same run; this figure is reported
+# beside it.
+FP64_PEAK_DERIVED_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12
 
 
 # DRAM bytes per system measured by ncu for the current kernels, keyed by
@@ -91,7 +93,8 @@ DRAM_BYTES_PER_SYSTEM = {}
 VARIANT_NAMES = {1: "k_factor_thread", 2: "k_factor_group<T=2>", 4: "k_factor_group<T=4>",
                  8: "k_factor_group<T=8>", 16: "k_factor_group<T=16>", 102: "k_smem_group<T=2>",
                  104: "k_smem_group<T=4>", 108: "k_smem_group<T=8>", 116: "k_smem_group<T=16>",
-                 132: "k_smem_group<T=32>"}
+                 132: "k_smem_group<T=32>", 202: "k_smem_group<T=2, walk>", 204: "k_smem_group<T=4, walk>",
+                 208: "k_smem_group<T=8, walk>"}
 
 
 def load_peaks():
@@ -316,7 +319,7 @@ NORTON_EVAL_FLOPS = 244
 NORTON_LU_FLOPS = flops_per_system(7)
 
 
-def newton_bench(tl, h, steps, warmup, torch, device, I, seed, npoints=NEWTON_POINTS, cpu_driven_steps=3):
+def newton_bench(tl, h, steps, warmup, torch, device, I, seed, peak, npoints=NEWTON_POINTS, cpu_driven_steps=3):
     """Norton Newton over npoints (n = 7): the fused per-point kernel
     (Algorithm 2) in points/s with its FP64 fraction, and the batched,
     CPU-driven loop (Algorithm 1) on the same points beside it."""
@@ -357,7 +360,7 @@ def newton_bench(tl, h, steps, warmup, torch, device, I, seed, npoints=NEWTON_PO
     out = {"points": npoints, "ms": med, "points_per_s": npoints / (med / 1e3),
            "mean_iterations": total_it / npoints, "max_iterations": int(iters.max().item()),
            "status_counts": status[:4], "fp64_tflops": flops / (med / 1e3) / 1e12,
-           "fp64_frac": flops / (med / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+           "fp64_frac": flops / (med / 1e3) / 1e12 / peak,
            "flops_model": "per solve 300 (LU n=7) + per law evaluation 244"}
     if cpu_driven_steps > 0:
         x_f, it_f, st_f = x.clone(), it.clone(), st.clone()
@@ -770,10 +773,24 @@ def main():
     data = make_sweep(n_list, 1, rank_seed(1236, rank), device, torch, L, I, args.batch)
     gen_s = time.perf_counter() - t_gen
 
+    # FP64 pipe rate of this GPU, measured before and after the timed sweep
+    # (independent DFMA chains on every SM); the faster is the roofline peak
+    peaks = []
+
+    def measure_peak():
+        st, tf, per_clk, mhz = tl.tl_measure_fma_peak(h, 64)
+        tl.check("tl_measure_fma_peak", st, h)
+        peaks.append({"tflops": tf, "dfma_lanes_per_clk_per_sm": per_clk, "sm_mhz": mhz})
+
+    measure_peak()
     log("timing interleaved sweep")
     with Clocks(local) as clk:
         step_ms, per_n = time_sweep(tl, h, data, 1, args.steps, args.warmup, torch, barrier)
     clocks = clk.summary()
+    measure_peak()
+    peak = max(p["tflops"] for p in peaks)
+    st32, fp32_tf, fp32_clk, _ = tl.tl_measure_fma_peak(h, 32)
+    tl.check("tl_measure_fma_peak", st32, h)
 
     med_step = max_over_ranks(statistics.median(step_ms), dist, device)
     systems_rank = sum(d["S"] for d in data.values())
@@ -787,7 +804,7 @@ def main():
         flops_total += f
         per_n_out[n] = {"batch": d["S"], "ms": round(ms, 4), "solves_per_s": d["S"] / (ms / 1e3),
                         "fp64_tflops": f / (ms / 1e3) / 1e12,
-                        "fp64_frac": f / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                        "fp64_frac": f / (ms / 1e3) / 1e12 / peak,
                         "gbs": bytes_per_system(n) * d["S"] / (ms / 1e3) / 1e9}
     # dominant kernel: the variant (thread-to-system mapping + storage) with
     # the largest share of the step; its largest launch is the roofline unit
@@ -804,17 +821,26 @@ def main():
     traffic = DRAM_BYTES_PER_SYSTEM.get((fam, dom))
     roofline = {"bound": "alu", "pipe": "fp64",
                 "kernel": f"{VARIANT_NAMES.get(fam, fam)} (variant {fam}), gesv n={dom} interleaved launch",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS,
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
                 "traffic": traffic * data[dom]["S"] if traffic else None,
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per system on a smaller batch "
                                   "of the same kernel and n, scaled to the launch" if traffic else
                                   "null: no ncu DRAM counters taken on the current version of this kernel",
-                "peak_source": "derived: 152 SMs x 4 SMSPs x 0.5 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25)",
+                "peak_source": "measured in this run by tl_measure_fma_peak (independent DFMA chains, 4 x 256 "
+                               "threads per SM, CUDA events), faster of the probes before and after the sweep",
+                "peak_probes": peaks,
+                "peak_derived": FP64_PEAK_DERIVED_TFLOPS,
+                "peak_derived_source": "152 SMs x 4 SMSPs x 0.5 DFMA/clk x 2 flop x 2.07 GHz",
+                "fp32_fma_peak_tflops": fp32_tf, "fp32_ffma_lanes_per_clk_per_sm": fp32_clk,
                 "kernel_share_of_step": fam_ms[fam] / sum(fam_ms.values()),
                 "kernel_n": fam_n,
-                "kernel_fp64_frac": fam_flops / (fam_ms[fam] / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
-                "sweep_fp64_frac": flops_total / (med_step / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
+                "kernel_fp64_frac": fam_flops / (fam_ms[fam] / 1e3) / 1e12 / peak,
+                "sweep_fp64_frac": flops_total / (med_step / 1e3) / 1e12 / peak,
+                # the per-n evidence for ">= 0.60 of the FP64 roofline for n >= 8"
+                "per_n_fp64_frac": [round(per_n_out[n]["fp64_frac"], 3) for n in sorted(per_n_out)],
+                "per_n_variant": [variant_of[n] for n in sorted(per_n_out)],
+                "per_n_first": min(per_n_out)}
     del data
     torch.cuda.empty_cache()
 
@@ -833,7 +859,8 @@ def main():
 
     if not args.no_newton:
         log("newton")
-        extra["newton"] = newton_bench(tl, h, max(2, args.steps // 2), 2, torch, device, I, rank_seed(1237, rank))
+        extra["newton"] = newton_bench(tl, h, max(2, args.steps // 2), 2, torch, device, I, rank_seed(1237, rank),
+                                       peak)
         extra["newton"]["points_per_s"] *= world
         torch.cuda.empty_cache()
 

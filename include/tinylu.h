@@ -321,13 +321,35 @@ tl_status tl_autotune(tl_handle *h, int n_min, int n_max, tl_layout layout,
                       const char *table_path);
 
 /*
+ * tl_measure_fma_peak -- measure the FMA throughput of the current device.
+ * The LU kernels are bound by the binary64 FMA pipe (Sec. 2.2: O(n^3) fused
+ * multiply-adds against O(n^2) bytes), so the pipe's measured rate is the
+ * roofline their throughput is compared with.  Launches 4 blocks of 256
+ * threads per SM, each thread running 8 independent FMA chains, three times
+ * on `stream` (the first warms up), and synchronizes the stream.
+ *   bits                64 (binary64 DFMA) or 32 (binary32 FFMA).
+ *   tflops              out (host): 2 x FMAs per second / 1e12 of the
+ *                       fastest timed launch (CUDA events).
+ *   fma_per_clk_per_sm  out (host, nullable): FMA lanes per SM per SM clock,
+ *                       from the SM cycle counter of the same launch.
+ *   sm_mhz              out (host, nullable): the SM clock the launch ran at.
+ * Allocates nothing; must not run during stream capture
+ * (TL_ERR_UNSUPPORTED).
+ */
+tl_status tl_measure_fma_peak(tl_handle *h, int bits, double *tflops, double *fma_per_clk_per_sm,
+                              double *sm_mhz, cudaStream_t stream);
+
+/*
  * tl_dispatch_set / tl_dispatch_get -- read or override the per-n dispatch
  * table that tl_autotune fills (the size-aware "best X" dispatcher of
  * Sec. 4.1).
  *   variant  lanes + 100 * storage: lanes per system (1 = one thread per
  *            system, 2, 4, 8, 16, 32), storage 0 = registers (a kernel
  *            compiled for that n; 1..16 lanes), 1 = shared memory (run-time
- *            n, n >= 2; 2..32 lanes).  0 restores the built-in default.  A
+ *            n, n >= 2; 2..32 lanes; the trailing update of 2..8 lanes on a
+ *            lane tile, of 16 and 32 lanes element by element), 2 = shared
+ *            memory with the element-by-element trailing update for 2..8
+ *            lanes.  0 restores the built-in default.  A
  *            variant not built for n is rejected with TL_ERR_INVALID_ARG
  *            (argument 4).
  *   block    0 (occupancy + wave-fill heuristic) or 32, 64, 128 threads.
@@ -420,9 +442,15 @@ typedef struct {
     int64_t ticks;
     int64_t points;       /* Newton points + solve systems completed */
     size_t arena_high_water;
+    double host_enqueue_s;  /* request-loop time spent forming and issuing ticks */
+    double kernel_busy_s;   /* time at least one of the server's kernels ran
+                               (union of the kernel intervals, CUDA events) */
 } tl_server_stats;
 
-/* Create a server on the handle's device (the handle must outlive it). */
+/* Create a server on the handle's device (the handle must outlive it).
+ * Each tick's bucket workspace for its solve requests comes out of the
+ * arena, so a running server allocates no device memory and never
+ * synchronizes the device. */
 tl_status tl_server_create(tl_handle *h, const tl_server_config *cfg, tl_server **out);
 /* Queue a request (the descriptor is copied); *id identifies it.  Invalid
  * descriptors return TL_ERR_INVALID_ARG (tl_last_bad_arg of the server's
@@ -437,6 +465,11 @@ tl_status tl_server_test(tl_server *s, int64_t id, int32_t *done, int32_t *req_s
  * request stays queued or running). */
 tl_status tl_server_wait(tl_server *s, int64_t id, double timeout_s, int32_t *req_status, double *latency_s);
 tl_status tl_server_stats_get(tl_server *s, tl_server_stats *out);
+/* Stop (paused != 0) or resume admitting queued requests into ticks.  Ticks
+ * already issued run to completion; submissions are still accepted and
+ * queued.  tl_server_destroy resumes admission so that every queued request
+ * finishes. */
+tl_status tl_server_pause(tl_server *s, int paused);
 /* Finish every queued request, stop the request loop, free the arena. */
 tl_status tl_server_destroy(tl_server *s);
 

@@ -48,7 +48,7 @@ IR_FAMILIES = (
 # smaller n run one thread per point).
 NEWTON_GROUP_FAMILIES = [(n, t) for n, t in KERNEL_FAMILIES if n >= 10]
 
-PLAIN_SOURCES = ["tl_api.cu", "tl_newton.cu", "tl_newton_cpu_driven.cu", "tl_ragged.cu", "tl_noalloc.cu", "tl_inst_smem.cu", "tl_autotune.cu", "tl_server.cu", "tl_newton_smem.cu"]
+PLAIN_SOURCES = ["tl_api.cu", "tl_newton.cu", "tl_newton_cpu_driven.cu", "tl_ragged.cu", "tl_noalloc.cu", "tl_inst_smem.cu", "tl_autotune.cu", "tl_server.cu", "tl_newton_smem.cu", "tl_peak.cu"]
 
 
 def _nvcc():

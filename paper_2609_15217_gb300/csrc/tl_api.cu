@@ -158,17 +158,17 @@ tl_status launch_variant(tl_handle *h, const Variant *v, int n, int block, Solve
 {
     if (args.batch == 0) return TL_OK;
     const int64_t threads = args.batch * v->lanes;
-    const size_t per_sys = v->kind == 1 ? smem_sys_bytes(n, v->lanes) : 0;
+    const size_t per_sys = v->kind >= 1 ? smem_sys_bytes(n, v->lanes) : 0;
     cudaError_t e;
     int dyn_limit = h->max_smem_per_block;
-    if (v->kind == 1) {
+    if (v->kind >= 1) {
         const tl_status st = smem_opt_in(h, v->kernel, &dyn_limit);
         if (st != TL_OK) return st;
     }
     if (block <= 0) block = pick_block(h, v->kernel, threads, v->lanes, per_sys, dyn_limit);
     const int64_t grid = (threads + block - 1) / block;
     if (grid > INT_MAX) return TL_ERR_UNSUPPORTED;
-    if (v->kind == 1) {
+    if (v->kind >= 1) {
         const size_t smem = (block / v->lanes) * per_sys;
         if (smem > static_cast<size_t>(dyn_limit)) return TL_ERR_UNSUPPORTED;
         int nn = n;

@@ -145,7 +145,7 @@ extern "C" tl_status tl_autotune(tl_handle *h, int n_min, int n_max, tl_layout l
             const Variant *v = &l.v[i];
             for (int block : {32, 64, 128}) {
                 if (block < v->lanes) continue;
-                if (v->kind == 1 && (block / v->lanes) * smem_sys_bytes(n, v->lanes) + 1024 > static_cast<size_t>(h->max_smem_per_block))
+                if (v->kind >= 1 && (block / v->lanes) * smem_sys_bytes(n, v->lanes) + 1024 > static_cast<size_t>(h->max_smem_per_block))
                     continue;
                 float ms_best = 1e30f;
                 for (int rep = 0; rep < 3; ++rep) {

@@ -77,7 +77,7 @@ enum : int {
     kOpNewtonTanh = 6
 };
 constexpr int kOps = 7;
-constexpr int kMaxVariants = 8;
+constexpr int kMaxVariants = 12;
 struct VariantList {
     int count;
     Variant v[kMaxVariants];

@@ -160,7 +160,7 @@ tl_status launch_binary64(tl_handle *h, int64_t batch, RaggedArgs &r, cudaStream
         const Choice &c = h->choice[nn][kPerSystem][kOpRagged];
         const Variant *v = find_variant(nn, kPerSystem, kOpRagged, c.lanes ? c.lanes : default_ragged_id(nn));
         if (!v) return TL_ERR_UNSUPPORTED;
-        if (v->kind == 1) {
+        if (v->kind >= 1) {
             const tl_status st = launch_smem_ragged(h, v, nn, batch, r, stream, smem_sys_bytes(nn, v->lanes));
             if (st != TL_OK) return st;
             continue;
@@ -210,7 +210,7 @@ tl_status ragged_solve(tl_handle *h, int64_t batch, const int32_t *n, RaggedArgs
         const Variant *v =
             find_variant(nn, kPerSystem, kOpRaggedIr, c.lanes ? c.lanes : default_ir_id(nn));
         if (!v) return TL_ERR_UNSUPPORTED;
-        if (v->kind == 1) {
+        if (v->kind >= 1) {
             const tl_status st = launch_smem_ragged(h, v, nn, batch, r, stream, ir_smem_bytes_per_system(nn));
             if (st != TL_OK) return st;
             continue;

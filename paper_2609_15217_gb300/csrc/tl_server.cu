@@ -72,11 +72,13 @@ struct Req {
         }
         return o - base;
     }
-    // tick-table bytes this request adds (job entry, or ragged arrays)
+    // tick-table bytes this request adds (job entry, or the ragged solve's
+    // per-system arrays: n, a_off, b_off, piv_off, info)
     size_t table_bytes() const
     {
         return d.kind == TL_REQ_NEWTON ? sizeof(NewtonJob) : static_cast<size_t>(d.count) * 32;
     }
+    int64_t systems() const { return d.kind == TL_REQ_SOLVE ? d.count : 0; }
 };
 
 // Requests of a tick that complete together: one Newton law class, all the
@@ -85,12 +87,22 @@ struct Req {
 struct Group {
     std::vector<Req *> reqs;
     bool done = false;
+    bool timed = false;  // kernel timing events recorded in kev[2g], kev[2g + 1]
 };
 constexpr int kMaxGroups = 2 * TL_MAX_N + 8;
+
+// Bytes of a tick's scratch block: the tables plus the bucket workspace of
+// the ragged solve over its `nsys` systems (so no tick ever grows a
+// workspace with cudaMalloc or synchronizes the device).
+size_t tick_scratch_bytes(size_t table, int64_t nsys)
+{
+    return table + (nsys > 0 ? up(ragged_ws_ints(nsys, false) * sizeof(int32_t)) : 0) + 4 * Arena::kAlign;
+}
 
 struct Slot {
     cudaStream_t stream = nullptr;
     std::vector<cudaEvent_t> evs;  // kMaxGroups events
+    std::vector<cudaEvent_t> kev;  // 2 * kMaxGroups timing events around each group's kernels
     tl_handle *h = nullptr;  // own handle: the ragged solve's workspace is per handle
     bool busy = false;
     std::vector<Req *> reqs;
@@ -118,8 +130,13 @@ struct tl_server {
     std::unordered_map<int64_t, Req *> reqs;
     int64_t next_id = 1;
     bool stop = false;
+    bool paused = false;
     tl_server_stats stats{};
     std::thread loop;
+    // kernel intervals (ms after t0_ev) of the completed groups
+    cudaEvent_t t0_ev = nullptr;
+    std::vector<std::pair<float, float>> kernel_spans;
+    double busy_union();
 
     void run();
     bool form_tick(Slot &sl, std::vector<Req *> &batch, size_t &scratch_off, size_t &scratch_bytes);
@@ -172,7 +189,7 @@ tl_status grow_stage(Slot &sl, size_t bytes)
 bool tl_server::form_tick(Slot &, std::vector<Req *> &batch, size_t &scratch_off, size_t &scratch_bytes)
 {
     const int64_t cap = cfg.max_points_per_tick;
-    int64_t pts = 0;
+    int64_t pts = 0, nsys = 0;
     size_t table = 0;
     while (!pending.empty() && batch.size() < kMaxJobsPerTick) {
         Req *r = pending.front();
@@ -184,10 +201,11 @@ bool tl_server::form_tick(Slot &, std::vector<Req *> &batch, size_t &scratch_off
         batch.push_back(r);
         pending.pop_front();
         pts += r->d.count;
+        nsys += r->systems();
         table += up(r->table_bytes());
     }
     while (!batch.empty()) {
-        scratch_bytes = table + 4 * Arena::kAlign;
+        scratch_bytes = tick_scratch_bytes(table, nsys);
         scratch_off = arena.alloc(scratch_bytes);
         if (scratch_off != SIZE_MAX) return true;
         Req *r = batch.back();  // give the last request back and retry
@@ -195,6 +213,7 @@ bool tl_server::form_tick(Slot &, std::vector<Req *> &batch, size_t &scratch_off
         arena.release(r->off, r->bytes);
         r->off = SIZE_MAX;
         table -= up(r->table_bytes());
+        nsys -= r->systems();
         pending.push_front(r);
     }
     return false;
@@ -224,12 +243,12 @@ tl_status tl_server::enqueue(Slot &sl, std::vector<Req *> &batch)
     }
     tl_status ts = grow_stage(sl, need + 4 * Arena::kAlign);
     if (ts != TL_OK) return ts;
-    auto close_group = [&](std::vector<Req *> &reqs) -> tl_status {
+    auto close_group = [&](std::vector<Req *> &reqs, bool timed) -> tl_status {
         const size_t g = sl.groups.size();
         if (g >= sl.evs.size()) return TL_ERR_UNSUPPORTED;
         const cudaError_t er = cudaEventRecord(sl.evs[g], st);
         if (er != cudaSuccess) return fail_cuda(sl.h, er);
-        sl.groups.push_back(Group{reqs, false});
+        sl.groups.push_back(Group{reqs, false, timed});
         return TL_OK;
     };
     auto copy_in = [&](Req *r) -> cudaError_t {
@@ -262,7 +281,7 @@ tl_status tl_server::enqueue(Slot &sl, std::vector<Req *> &batch)
         return er;
     };
 
-    if (!empties.empty() && (ts = close_group(empties)) != TL_OK) return ts;
+    if (!empties.empty() && (ts = close_group(empties, false)) != TL_OK) return ts;
     size_t cur = 0;  // offset inside both the staging buffer and the scratch block
     for (auto &kv : classes) {
         for (Req *r : kv.second)
@@ -293,12 +312,16 @@ tl_status tl_server::enqueue(Slot &sl, std::vector<Req *> &batch)
         B.total = start;
         B.rtol = cfg.rtol;
         B.max_iter = cfg.max_iter;
+        const size_t g = sl.groups.size();
+        if (g >= sl.evs.size()) return TL_ERR_UNSUPPORTED;
+        cudaEventRecord(sl.kev[2 * g], st);
         ts = newton_launch(sl.h, kv.first.first, kv.first.second, B, st);
         if (ts != TL_OK) return ts;
+        cudaEventRecord(sl.kev[2 * g + 1], st);
         cur += tb;
         for (Req *r : kv.second)
             if ((e = copy_out(r)) != cudaSuccess) return fail_cuda(sl.h, e);
-        if ((ts = close_group(kv.second)) != TL_OK) return ts;
+        if ((ts = close_group(kv.second, true)) != TL_OK) return ts;
     }
     if (nsys > 0) {
         for (Req *r : solves)
@@ -310,6 +333,7 @@ tl_status tl_server::enqueue(Slot &sl, std::vector<Req *> &batch)
         int64_t *hb = ha + nsys;
         int64_t *hp = hb + nsys;
         const size_t o_n = cur, o_a = cur + up(nsys * 4), o_info = o_a + up(nsys * 24);
+        const size_t o_ws = o_info + up(nsys * 4);
         size_t q = 0;
         for (Req *r : solves) {
             const int64_t n = r->d.n;
@@ -326,10 +350,17 @@ tl_status tl_server::enqueue(Slot &sl, std::vector<Req *> &batch)
         const int64_t *da = reinterpret_cast<const int64_t *>(dptr(sl.scratch_off + o_a));
         int32_t *dinfo = reinterpret_cast<int32_t *>(dptr(sl.scratch_off + o_info));
         const double *dbase = reinterpret_cast<const double *>(base);
-        ts = tl_lupp_solve_batched(sl.h, static_cast<int64_t>(nsys), dn, da, dbase, da + nsys, dbase,
-                                   reinterpret_cast<double *>(base), da + 2 * nsys, reinterpret_cast<int32_t *>(base),
-                                   dinfo, TL_PREC_FP64, nullptr, st);
+        // the ragged solve of tl_lupp_solve_batched (binary64) with its bucket
+        // workspace in this tick's scratch block
+        RaggedArgs ra{nullptr, nullptr, da, dbase, da + nsys, dbase, reinterpret_cast<double *>(base),
+                      da + 2 * nsys, reinterpret_cast<int32_t *>(base), dinfo};
+        int32_t *dws = reinterpret_cast<int32_t *>(dptr(sl.scratch_off + o_ws));
+        const size_t g = sl.groups.size();
+        if (g >= sl.evs.size()) return TL_ERR_UNSUPPORTED;
+        cudaEventRecord(sl.kev[2 * g], st);
+        ts = ragged_solve(sl.h, static_cast<int64_t>(nsys), dn, ra, dws, st);
         if (ts != TL_OK) return ts;
+        cudaEventRecord(sl.kev[2 * g + 1], st);
         q = 0;
         for (Req *r : solves) {
             const size_t c = static_cast<size_t>(r->d.count);
@@ -338,14 +369,22 @@ tl_status tl_server::enqueue(Slot &sl, std::vector<Req *> &batch)
             if (e != cudaSuccess) return fail_cuda(sl.h, e);
             q += c;
         }
-        if ((ts = close_group(solves)) != TL_OK) return ts;
+        if ((ts = close_group(solves, true)) != TL_OK) return ts;
     }
     return TL_OK;
 }
 
 // Called with mu held: one group of a tick ended with `status`.
-void tl_server::finish_group(Slot &, Group &g, int32_t status)
+void tl_server::finish_group(Slot &sl, Group &g, int32_t status)
 {
+    const size_t gi = static_cast<size_t>(&g - sl.groups.data());
+    if (status == TL_OK && gi < sl.groups.size() && 2 * gi + 1 < sl.kev.size() && g.timed) {
+        float a = 0.f, b = 0.f;
+        if (cudaEventElapsedTime(&a, t0_ev, sl.kev[2 * gi]) == cudaSuccess &&
+            cudaEventElapsedTime(&b, t0_ev, sl.kev[2 * gi + 1]) == cudaSuccess && b >= a)
+            kernel_spans.emplace_back(a, b);
+        cudaGetLastError();
+    }
     const Clock::time_point now = Clock::now();
     for (Req *r : g.reqs) {
         r->done = true;
@@ -414,7 +453,8 @@ void tl_server::run()
                 break;
             }
         bool launched = false;
-        if (free_slot && !pending.empty()) {
+        if (free_slot && !pending.empty() && !paused) {
+            const Clock::time_point t_host = Clock::now();
             std::vector<Req *> batch;
             size_t soff = SIZE_MAX, sbytes = 0;
             if (form_tick(*free_slot, batch, soff, sbytes)) {
@@ -428,6 +468,7 @@ void tl_server::run()
                 lk.unlock();
                 const tl_status ts = enqueue(sl, batch);
                 lk.lock();
+                stats.host_enqueue_s += std::chrono::duration<double>(Clock::now() - t_host).count();
                 if (ts != TL_OK) {
                     // whatever was issued drains before the slot is reused
                     cudaStreamSynchronize(sl.stream);
@@ -449,7 +490,7 @@ void tl_server::run()
         }
         if (launched) continue;
         if (any_busy) cv_work.wait_for(lk, std::chrono::microseconds(20));
-        else cv_work.wait(lk, [&] { return stop || !pending.empty(); });
+        else cv_work.wait(lk, [&] { return stop || (!pending.empty() && !paused); });
     }
 }
 
@@ -474,12 +515,24 @@ extern "C" tl_status tl_server_create(tl_handle *h, const tl_server_config *cfg,
     }
     s->arena.reset(cfg->budget_bytes);
     s->slots.resize(static_cast<size_t>(cfg->slots));
+    bool t0_ok = cudaEventCreate(&s->t0_ev) == cudaSuccess && cudaEventRecord(s->t0_ev, nullptr) == cudaSuccess &&
+                 cudaEventSynchronize(s->t0_ev) == cudaSuccess;
+    if (!t0_ok) {
+        cudaGetLastError();
+        tl_server_destroy(s);
+        return TL_ERR_CUDA;
+    }
     for (Slot &sl : s->slots) {
         bool ok = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess && tl_create(&sl.h) == TL_OK;
         for (int g = 0; ok && g < kMaxGroups; ++g) {
             cudaEvent_t ev = nullptr;
             ok = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
             if (ok) sl.evs.push_back(ev);
+        }
+        for (int g = 0; ok && g < 2 * kMaxGroups; ++g) {
+            cudaEvent_t ev = nullptr;
+            ok = cudaEventCreate(&ev) == cudaSuccess;
+            if (ok) sl.kev.push_back(ev);
         }
         if (!ok) {
             cudaGetLastError();
@@ -501,7 +554,7 @@ extern "C" tl_status tl_server_submit(tl_server *s, const tl_request *req, int64
     r->d = *req;
     if (req->kind == TL_REQ_NEWTON) law_params(req->law, &r->job);
     r->bytes = r->layout(0);
-    if (r->bytes + up(r->table_bytes()) + 4 * Arena::kAlign > s->arena.capacity()) {
+    if (r->bytes + tick_scratch_bytes(up(r->table_bytes()), r->systems()) > s->arena.capacity()) {
         delete r;
         return TL_ERR_NO_MEMORY;
     }
@@ -559,11 +612,41 @@ extern "C" tl_status tl_server_wait(tl_server *s, int64_t id, double timeout_s, 
     return report(s, s->reqs.find(id), req_status, latency_s);
 }
 
+// Called with mu held: the union of the recorded kernel intervals (the time
+// at least one of the server's kernels ran), in seconds.
+double tl_server::busy_union()
+{
+    if (kernel_spans.empty()) return 0.0;
+    std::sort(kernel_spans.begin(), kernel_spans.end());
+    double busy = 0.0;
+    float a = kernel_spans[0].first, b = kernel_spans[0].second;
+    for (size_t i = 1; i < kernel_spans.size(); ++i) {
+        if (kernel_spans[i].first > b) {
+            busy += b - a;
+            a = kernel_spans[i].first;
+        }
+        b = std::max(b, kernel_spans[i].second);
+    }
+    return (busy + (b - a)) * 1e-3;
+}
+
+extern "C" tl_status tl_server_pause(tl_server *s, int paused)
+{
+    if (!s) return TL_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->paused = paused != 0;
+    }
+    s->cv_work.notify_all();
+    return TL_OK;
+}
+
 extern "C" tl_status tl_server_stats_get(tl_server *s, tl_server_stats *out)
 {
     if (!s || !out) return TL_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(s->mu);
     *out = s->stats;
+    out->kernel_busy_s = s->busy_union();
     out->arena_high_water = s->arena.high_water();
     return TL_OK;
 }
@@ -574,17 +657,20 @@ extern "C" tl_status tl_server_destroy(tl_server *s)
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
+        s->paused = false;  // queued requests still finish
     }
     s->cv_work.notify_all();
     if (s->loop.joinable()) s->loop.join();
     for (Slot &sl : s->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
         for (cudaEvent_t ev : sl.evs) cudaEventDestroy(ev);
+        for (cudaEvent_t ev : sl.kev) cudaEventDestroy(ev);
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.h) tl_destroy(sl.h);
         if (sl.stage) cudaFreeHost(sl.stage);
     }
     cudaFree(s->base);
+    if (s->t0_ev) cudaEventDestroy(s->t0_ev);
     for (auto &kv : s->reqs) delete kv.second;
     delete s;
     return TL_OK;

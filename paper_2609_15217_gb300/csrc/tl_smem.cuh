@@ -43,13 +43,18 @@ constexpr int kSmemRowUnroll = TL_SMEM_ROW_UNROLL;
 // per SM).
 __host__ __device__ constexpr int smem_row_stride(int n) { return (n + 1) | 1; }
 
-// Shared-memory footprint of one system in doubles: the n x RS block, 32
-// reciprocals, 32 pivots (16 doubles).  Padded so that consecutive systems
-// start T slots apart modulo 16 (the systems of one half-warp then do not
-// collide on a bank).
+// Offsets (in doubles) of the n reciprocals RN(1/u_kk) and of the n pivot
+// rows (int32, two per double) behind a system's n x RS block.
+__host__ __device__ constexpr int smem_rcp_offset(int n) { return n * smem_row_stride(n); }
+__host__ __device__ constexpr int smem_piv_offset(int n) { return n * smem_row_stride(n) + n; }
+
+// Shared-memory footprint of one system in doubles: the n x RS block, n
+// reciprocals, n pivots.  Padded so that consecutive systems start T slots
+// apart modulo 16 (the systems of one half-warp then do not collide on a
+// bank).
 __host__ __device__ constexpr int smem_sys_doubles(int n, int T = 16)
 {
-    const int base = n * smem_row_stride(n) + 32 + 16;
+    const int base = smem_piv_offset(n) + (n + 1) / 2;
     const int want = (T < 16) ? T : 0;
     return base + ((want - base % 16) % 16 + 16) % 16;
 }
@@ -68,27 +73,29 @@ __device__ __forceinline__ int group_any_int(int v)
 
 // Elimination of one system held by the T lanes of a group: the augmented
 // n x (n+1) block M (row stride RS; column n = b when SOLVE), followed by
-// 32 reciprocals and 32 pivot rows.  LUpp with the arithmetic of the
+// n reciprocals and n pivot rows.  LUpp with the arithmetic of the
 // register solvers (negated multipliers a_ik * (-RN(1/a_kk)), one FMA per
 // update in increasing k, b carried as column n, back substitution by
 // RN(1/u_ii)); on return M holds L (negated, below the diagonal) and U, and
 // column n holds x when SOLVE.  Returns info.  Every lane of the warp must
 // call it together (shuffles and votes inside).
 //
-// Trailing updates use a TR x TC tile of lanes: lane (tr, tc) updates
-// rows k+1+tr, k+1+tr+TR, ... and columns k+1+tc, k+1+tc+TC, ..., keeping
-// its columns of the pivot row in registers.
-template <int T, bool SOLVE>
+// Trailing updates either walk the trailing block element by element (WALK:
+// lane t takes every T-th element, row-major) or use a TR x TC tile of
+// lanes: lane (tr, tc) updates rows k+1+tr, k+1+tr+TR, ... and columns
+// k+1+tc, k+1+tc+TC, ..., keeping its columns of the pivot row in registers.
+template <int T, bool SOLVE, bool WALK = (T >= 16)>
 __device__ __forceinline__ int smem_lupp(double *M, int n, int RS, int t, int tile, double threshold)
 {
     constexpr int MODE = SOLVE ? kGesv : kGetrf;
-    constexpr int TC = (T >= 4) ? 4 : T;  // lane tile (T <= 8; 16 and 32 lanes walk elements)
+    constexpr int TC = WALK ? 1 : (T >= 4) ? 4 : T;  // lane tile (when not walking elements)
     constexpr int TR = T / TC;
     constexpr int MAXC = TL_MAX_N / TC;  // whole column chunks per lane (at most 32 live columns)
-    static_assert(MAXC <= 16, "the chunk switch below covers 16 chunks");
+    static_assert(WALK || MAXC <= 16, "the chunk switch below covers 16 chunks");
+    static_assert(T >= 1 && T <= 32 && (32 % T) == 0, "T must divide 32");
     const int tr = t / TC, tc = t % TC;
-    double *rcp = M + n * RS;                              // 32 doubles
-    int *piv = reinterpret_cast<int *>(rcp + 32);          // 32 ints
+    double *rcp = M + n * RS;                              // n doubles
+    int *piv = reinterpret_cast<int *>(rcp + n);           // n ints
     int info = 0;
     bool tiny = false;
     const int wcols = n + (MODE == kGesv ? 1 : 0);         // columns incl. b
@@ -149,8 +156,8 @@ __device__ __forceinline__ int smem_lupp(double *M, int n, int RS, int t, int ti
         }
         __syncwarp();
         // a5 (+ forward part of a6 through column n): a_ij += (-l_ik) u_kj.
-        if (!zero && T >= 16) {
-            // 16 or 32 lanes per system: the R x C trailing block (R = n-k-1
+        if (!zero && WALK) {
+            // element walk: the R x C trailing block (R = n-k-1
             // rows, C live columns) is walked row-major, lane t taking the
             // elements t, t+T, t+2T, ...; every lane issues ceil(R C / T)
             // FMAs, the least any split can (a TR x TC lane tile issues
@@ -244,7 +251,8 @@ __device__ __forceinline__ int smem_lupp(double *M, int n, int RS, int t, int ti
 }
 
 // MODE: kGesv (A const, b -> x, LU optional by KEEP) or kGetrf (A in place).
-template <int T, int LAYOUT, int MODE, bool KEEP>
+// WALK: element walk of the trailing update instead of the lane tile.
+template <int T, int LAYOUT, int MODE, bool KEEP, bool WALK = (T >= 16)>
 __global__ void __launch_bounds__(128) k_smem_group(SolveArgs args, int n)
 {
     extern __shared__ double smem[];
@@ -301,13 +309,13 @@ __global__ void __launch_bounds__(128) k_smem_group(SolveArgs args, int n)
     const int64_t s = s0 + q;
     const bool active = s < args.batch;
     double *M = smem + q * per;
-    const int *piv = reinterpret_cast<const int *>(M + n * RS + 32);  // pivots (after 32 reciprocals)
+    const int *piv = reinterpret_cast<const int *>(M + smem_piv_offset(n));  // pivots (after n reciprocals)
     // non-finite entries anywhere in this system (loaded by threads q + SB*t')
     int badv = 0;
     for (int tp = t; tp < T; tp += T) badv |= s_bad[q + SB * tp];
     const bool bad = group_any_int<T>(badv) != 0;
 
-    const int info0 = smem_lupp<T, MODE == kGesv>(M, n, RS, t, args.tile, args.threshold);
+    const int info0 = smem_lupp<T, MODE == kGesv, WALK>(M, n, RS, t, args.tile, args.threshold);
     int info = info0;
     if (bad) info = -1;
 
@@ -393,7 +401,7 @@ __global__ void __launch_bounds__(128) k_smem_ragged(RaggedArgs r, int n)
         if (bad) info = -1;
         if (active) {
             const int64_t sidx = r.bucket[beg + base + q];
-            const int *piv = reinterpret_cast<const int *>(M + n * RS + 32);
+            const int *piv = reinterpret_cast<const int *>(M + smem_piv_offset(n));
             double *x = r.x + r.b_off[sidx];
             int32_t *ip = r.ipiv + r.piv_off[sidx];
             for (int i = t; i < n; i += T) {

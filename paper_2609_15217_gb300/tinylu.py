@@ -50,7 +50,8 @@ class tl_server_config(C.Structure):
 
 class tl_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("ticks", C.c_int64),
-                ("points", C.c_int64), ("arena_high_water", C.c_size_t)]
+                ("points", C.c_int64), ("arena_high_water", C.c_size_t), ("host_enqueue_s", C.c_double),
+                ("kernel_busy_s", C.c_double)]
 
 _SIGS = {
     "tl_create": ([C.POINTER(_vp)], _int),
@@ -76,8 +77,11 @@ _SIGS = {
     "tl_server_test": ([_vp, _i64, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_double)], _int),
     "tl_server_wait": ([_vp, _i64, C.c_double, C.POINTER(C.c_int32), C.POINTER(C.c_double)], _int),
     "tl_server_stats_get": ([_vp, C.POINTER(tl_server_stats)], _int),
+    "tl_server_pause": ([_vp, _int], _int),
     "tl_server_destroy": ([_vp], _int),
     "tl_dispatch_set": ([_vp, _int, _int, _int, _int], _int),
+    "tl_measure_fma_peak": ([_vp, _int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double), _vp],
+                            _int),
     "tl_dispatch_get": ([_vp, _int, _int, C.POINTER(_int), C.POINTER(_int)], _int),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -231,6 +235,13 @@ def tl_dispatch_get(h, n, layout):
     return st, v.value, b.value
 
 
+def tl_measure_fma_peak(h, bits=64, stream=None):
+    """Returns (status, TFLOP/s, FMA lanes per SM per clock, SM MHz)."""
+    tf, per_clk, mhz = C.c_double(0.0), C.c_double(0.0), C.c_double(0.0)
+    st = _lib.tl_measure_fma_peak(h, bits, C.byref(tf), C.byref(per_clk), C.byref(mhz), _stream(stream))
+    return st, tf.value, per_clk.value, mhz.value
+
+
 def make_request(kind, count, in_, x, i1, i2, law=None, n=0, rhs=None, aux=None, ld_in=0):
     """A tl_request over host arrays (numpy arrays or raw addresses)."""
     r = tl_request()
@@ -279,14 +290,19 @@ def tl_server_stats_get(s):
     return st, {k: getattr(out, k) for k, _ in tl_server_stats._fields_}
 
 
+def tl_server_pause(s, paused=True):
+    return _lib.tl_server_pause(s, 1 if paused else 0)
+
+
 def tl_server_destroy(s):
     return _lib.tl_server_destroy(s)
 
 
-def variant_id(lanes, shared=False):
+def variant_id(lanes, shared=False, walk=False):
     """Dispatch id of a kernel variant: lanes per system + 100 for the
-    shared-memory storage."""
-    return lanes + (100 if shared else 0)
+    shared-memory storage (+ 200 instead for the shared-memory solver whose
+    2..8 lanes walk the trailing update element by element)."""
+    return lanes + (200 if walk else 100 if shared else 0)
 
 
 def library():

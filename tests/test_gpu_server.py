@@ -161,15 +161,19 @@ def test_budget_refusals_and_timeouts(tl, h):
             assert tl.tl_server_test(srv, rid)[0] == tl.TL_ERR_INVALID_ARG   # released
         st, stats = tl.tl_server_stats_get(srv)
         assert stats["arena_high_water"] <= 4 << 20 and stats["completed"] == 6
-        # a zero wait on a request still running times out, then completes
+        # a request queued while admission is paused cannot be done: a zero
+        # and a short wait both time out, it stays queued, and it completes
+        # once admission resumes
         slow = Newton(tl, tl.TL_LAW_TANH, 13, 1500, 61)    # ~2.5 MiB: fits the arena
         sreq = slow.request(tl)
+        assert tl.tl_server_pause(srv, True) == tl.TL_OK
         st, rid = tl.tl_server_submit(srv, sreq)
         assert st == tl.TL_OK
-        st0, _, _ = tl.tl_server_wait(srv, rid, 0.0)
-        assert st0 in (tl.TL_ERR_TIMEOUT, tl.TL_OK)
-        if st0 == tl.TL_ERR_TIMEOUT:
-            assert tl.tl_server_wait(srv, rid, 120.0)[0] == tl.TL_OK
+        assert tl.tl_server_wait(srv, rid, 0.0)[0] == tl.TL_ERR_TIMEOUT
+        assert tl.tl_server_wait(srv, rid, 0.05)[0] == tl.TL_ERR_TIMEOUT
+        assert tl.tl_server_test(srv, rid)[:2] == (tl.TL_OK, 0)
+        assert tl.tl_server_pause(srv, False) == tl.TL_OK
+        assert tl.tl_server_wait(srv, rid, 120.0)[:2] == (tl.TL_OK, tl.TL_OK)
         # an empty request completes
         empty = tl.make_request(tl.TL_REQ_NEWTON, 0, None, None, None, None, law=tl.make_law(tl.TL_LAW_NORTON, 7,
                                 tuple(oracle.norton_params())))
@@ -186,3 +190,39 @@ def test_create_errors(tl, h):
     assert tl.tl_server_create(h, 1 << 10, 2, 100)[0] == tl.TL_ERR_INVALID_ARG
     assert tl.tl_server_create(h, 1 << 24, 0, 100)[0] == tl.TL_ERR_INVALID_ARG
     assert tl.tl_server_create(h, 1 << 24, 2, -1)[0] == tl.TL_ERR_INVALID_ARG
+
+
+def test_solve_ticks_allocate_no_device_memory(tl, h):
+    # every tick takes its ragged-solve workspace from the arena: a second,
+    # larger solve tick leaves the device's free memory unchanged
+    st, srv = tl.tl_server_create(h, 256 << 20, 2, 1 << 20)
+    assert st == tl.TL_OK
+    try:
+        small, large = Solve(12, 200, 71), Solve(20, 60000, 72)
+        st, rid = tl.tl_server_submit(srv, small.request(tl))
+        assert st == tl.TL_OK and tl.tl_server_wait(srv, rid, 120.0)[:2] == (tl.TL_OK, tl.TL_OK)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        lreq = large.request(tl)
+        st, rid = tl.tl_server_submit(srv, lreq)
+        assert st == tl.TL_OK and tl.tl_server_wait(srv, rid, 120.0)[:2] == (tl.TL_OK, tl.TL_OK)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        st, stats = tl.tl_server_stats_get(srv)
+        assert stats["kernel_busy_s"] > 0 and stats["host_enqueue_s"] > 0
+    finally:
+        assert tl.tl_server_destroy(srv) == tl.TL_OK
+    small.check(tl, h)
+    large.check(tl, h)
+
+
+def test_pause_then_destroy_finishes_queued(tl, h):
+    st, srv = tl.tl_server_create(h, 64 << 20, 1, 1 << 16)
+    assert st == tl.TL_OK
+    w = Solve(7, 500, 73)
+    req = w.request(tl)
+    assert tl.tl_server_pause(srv, True) == tl.TL_OK
+    st, rid = tl.tl_server_submit(srv, req)
+    assert st == tl.TL_OK
+    assert tl.tl_server_destroy(srv) == tl.TL_OK     # resumes admission, drains the queue
+    w.check(tl, h)

@@ -34,16 +34,17 @@ def h(tl):
     tl.tl_destroy(hh)
 
 
-@pytest.mark.parametrize("lanes", [2, 4, 8, 16, 32])
+@pytest.mark.parametrize("lanes,walk", [(2, False), (4, False), (8, False), (16, False), (32, False),
+                                        (2, True), (4, True), (8, True)])
 @pytest.mark.parametrize("n", [2, 3, 7, 9, 10, 13, 16, 17, 24, 25, 31, 32])
-def test_shared_memory_variants(tl, h, n, lanes):
+def test_shared_memory_variants(tl, h, n, lanes, walk):
     batch = 3 * 64 + 11
     A, b, _, _ = inputs.sweep_systems(n, batch, inputs.config_seed(2, n) + 7)
     A[3, :, 1] = 0.0            # a zero pivot
     A[5, n - 1, n - 1] = np.nan  # a non-finite system
     x_o, piv_o, info_o, _, LU_o = oracle.gesv(A, b, want_lu=True)
     for layout in (0, 1):
-        vid = tl.variant_id(lanes, shared=True)
+        vid = tl.variant_id(lanes, shared=True, walk=walk)
         assert tl.tl_dispatch_set(h, n, layout, vid, 0) == tl.TL_OK
         assert tl.tl_dispatch_get(h, n, layout)[1] == vid
         x_g, piv_g, info_g, LU_g = gpu_gesv(tl, h, A, b, layout)
