@@ -449,13 +449,8 @@ def ragged_bench(tl, h, steps, warmup, torch, device, I, seed, batch=RAGGED_BATC
                        "half U[-1,1], half kappa in [1e2,1e8], b = A x_true; per-system column-major, sizes "
                        "mixed in memory; one tl_lupp_solve_batched call",
            "bytes_A": d["A"].numel() * 8}
-    for name, prec in (("fp64", tl.TL_PREC_FP64), ("fp32_ir", tl.TL_PREC_FP32_IR)):
-        def run():
-            st = tl.tl_lupp_solve_batched(h, batch, d["sizes"], d["a_off"], d["A"], d["b_off"], d["b"], x,
-                                          d["b_off"], ipiv, info, prec, ref if prec else None,
-                                          stream.cuda_stream)
-            if st != 0:
-                tl.check("tl_lupp_solve_batched", st, h)
+
+    def timed(run):
         for _ in range(warmup):
             run()
         torch.cuda.synchronize()
@@ -468,17 +463,63 @@ def ragged_bench(tl, h, steps, warmup, torch, device, I, seed, batch=RAGGED_BATC
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
-        med = statistics.median(ms)
+        return statistics.median(ms)
+
+    legs = (("fp64", tl.TL_PREC_FP64, tl.TL_RAGGED_PERSISTENT),
+            ("fp64_per_size_launches", tl.TL_PREC_FP64, tl.TL_RAGGED_PER_SIZE),
+            ("fp32_ir", tl.TL_PREC_FP32_IR, tl.TL_RAGGED_PERSISTENT))
+    piv_ref = None
+    for name, prec, mode in legs:
+        def run():
+            st = tl.tl_lupp_solve_batched(h, batch, d["sizes"], d["a_off"], d["A"], d["b_off"], d["b"], x,
+                                          d["b_off"], ipiv, info, prec, ref if prec else None,
+                                          stream.cuda_stream)
+            if st != 0:
+                tl.check("tl_lupp_solve_batched", st, h)
+        tl.check("tl_ragged_set_mode", tl.tl_ragged_set_mode(h, mode), h)
+        med = timed(run)
+        tl.tl_ragged_set_mode(h, tl.TL_RAGGED_PERSISTENT)
         be, fe = ragged_errors(d, x, torch)
         out[name] = {"ms": med, "solves_per_s": batch / (med / 1e3), "max_backward_error_n_eps": be,
                      "max_forward_error_vs_x_true": fe,
-                     "info_nonzero": int((info != 0).sum().item())}
+                     "info_nonzero": int((info != 0).sum().item()),
+                     "launches": "bucketing (3) + plan + 1 persistent" if mode == tl.TL_RAGGED_PERSISTENT
+                                 else "bucketing (3) + 32 per-size"}
         if prec:
             hist = torch.bincount((ref + 1).to(torch.int64), minlength=5).tolist()
             out[name]["refine_steps_hist"] = {"fallback": hist[0], "0": hist[1], "1": hist[2], "2": hist[3],
                                               "3": hist[4]}
+        elif piv_ref is None:
+            piv_ref = ipiv.clone()
+        else:
+            out[name]["pivots_equal_persistent"] = bool(torch.equal(ipiv, piv_ref))
+    # the same systems as homogeneous per-n batches (bucketed and copied into
+    # contiguous per-system arrays outside the timed region), one
+    # tl_gesv_batched launch per size with the tuned per-n kernels
+    per_n = {}
+    for n, (idx, ia, ib) in d["buckets"].items():
+        S = idx.numel()
+        per_n[n] = dict(S=S, A=d["A"][ia].contiguous(), b=d["b"][ib].contiguous(),
+                        x=torch.empty(S * n, dtype=torch.float64, device=device),
+                        p=torch.empty(S * n, dtype=torch.int32, device=device),
+                        i=torch.empty(S, dtype=torch.int32, device=device))
+
+    def run_plain():
+        for n, q in per_n.items():
+            st = tl.tl_gesv_batched(h, n, q["A"], None, q["b"], q["x"], q["p"], q["i"], 0, q["S"], q["S"],
+                                    stream.cuda_stream)
+            if st != 0:
+                tl.check("tl_gesv_batched", st, h)
+    med = timed(run_plain)
+    same = all(torch.equal(q["p"], piv_ref[d["buckets"][n][2]]) for n, q in per_n.items())
+    out["fp64_plain_per_n_gesv"] = {"ms": med, "solves_per_s": batch / (med / 1e3),
+                                    "launches": f"{len(per_n)} tl_gesv_batched (+ fixup passes)",
+                                    "pivots_equal_persistent": same,
+                                    "inputs": "pre-bucketed contiguous per-n copies (bucketing not timed)"}
+    out["persistent_vs_plain_per_n"] = out["fp64_plain_per_n_gesv"]["ms"] / out["fp64"]["ms"]
+    out["persistent_vs_per_size_launches"] = out["fp64_per_size_launches"]["ms"] / out["fp64"]["ms"]
     out["fp32_ir_speedup"] = out["fp64"]["ms"] / out["fp32_ir"]["ms"]
-    del d
+    del d, per_n
     return out
 
 

@@ -114,6 +114,19 @@ tl_status tl_last_cuda_error(tl_handle *h, int *err);
 int tl_last_bad_arg(tl_handle *h);
 
 /*
+ * tl_check_bounds_violations -- the bounds-checked build of the library
+ * (libtinylu_checked.so: the C ABI of the fixed-size and ragged solves with
+ * the shared-memory solvers compiled with -DTL_CHECK_BOUNDS) checks every
+ * shared-memory index of the element-walk elimination and of the loads
+ * into shared memory against its system's block; a violation is counted
+ * and the access redirected inside the block (no trap, no fault).  This
+ * call synchronizes the device and returns in *count (host) the violations
+ * counted since the last call, then clears the counters.  The normal
+ * library has no checks and returns TL_ERR_UNSUPPORTED.
+ */
+tl_status tl_check_bounds_violations(unsigned long long *count);
+
+/*
  * tl_getrf_batched -- LUpp factorization in place (Sec. 2.2, PA = LU).
  *   n      1..32
  *   A      in: the batch of matrices; out: L (unit lower, strictly below the
@@ -206,14 +219,32 @@ tl_status tl_gesv_batched_tilepiv(tl_handle *h, int n, int tile, double threshol
  * Systems are bucketed by n on the device in the handle's workspace (grown
  * on demand with cudaMalloc; a call that would need to grow it while the
  * stream is being captured returns TL_ERR_NO_MEMORY; 4 bytes per system,
- * 8 with TL_PREC_FP32_IR) and solved by per-n persistent launches; with
- * TL_PREC_FP32_IR the systems handed back go through the binary64 kernels
- * afterwards.  No host synchronization.  batch must be below 2^31.
+ * 8 with TL_PREC_FP32_IR, plus 1 KiB) and, in the default mode, the binary64
+ * solves of every size run in ONE persistent launch (warps take work items
+ * of one size class from a device counter, largest n first; lanes per
+ * system per n from the dispatch table's shared-memory ragged variant, see
+ * tl_dispatch_set); with TL_PREC_FP32_IR the systems handed back go through
+ * that binary64 launch afterwards.  No host synchronization.  batch must be
+ * below 2^31.
  */
 tl_status tl_lupp_solve_batched(tl_handle *h, int64_t batch, const int32_t *n, const int64_t *a_off,
                                 const double *A, const int64_t *b_off, const double *b, double *x,
                                 const int64_t *piv_off, int32_t *ipiv, int32_t *info,
                                 tl_precision prec, int32_t *refine_steps, cudaStream_t stream);
+
+/*
+ * tl_ragged_set_mode -- how tl_lupp_solve_batched (and its no-allocation
+ * form) runs the binary64 solves of a ragged batch:
+ *   TL_RAGGED_PERSISTENT  one persistent launch over every size class
+ *                         (default; Sec. 2.3 batching with the work of all
+ *                         sizes fused into one kernel).
+ *   TL_RAGGED_PER_SIZE    one launch per size class 1..32 with the per-n
+ *                         kernels of tl_gesv_batched (the comparator of the
+ *                         single launch).
+ * Results are identical in both modes.  Other values: TL_ERR_INVALID_ARG.
+ */
+typedef enum { TL_RAGGED_PERSISTENT = 0, TL_RAGGED_PER_SIZE = 1 } tl_ragged_mode;
+tl_status tl_ragged_set_mode(tl_handle *h, int mode);
 
 /*
  * tl_lupp_solve_batched_noalloc -- the ragged solve of tl_lupp_solve_batched
@@ -231,7 +262,7 @@ tl_status tl_lupp_solve_batched(tl_handle *h, int64_t batch, const int32_t *n, c
  *   batch  at most TL_NOALLOC_MAX_BATCH systems; a larger batch returns
  *          TL_ERR_INVALID_ARG with tl_last_bad_arg() == 2 and launches
  *          nothing.  Other arguments and results as tl_lupp_solve_batched.
- *   The scratch array (TL_NOALLOC_MAX_BATCH + 192 int32, about 4 MiB) exists
+ *   The scratch array (TL_NOALLOC_MAX_BATCH + 256 int32, about 4 MiB) exists
  *   on every GPU that loads the library, from load until process exit.
  *   The first call with a given device current looks up the array's device
  *   address (cudaGetSymbolAddress) and caches it; make that first call

@@ -11,12 +11,26 @@
 #include <new>
 #include <unordered_map>
 
+#include <vector>
+
 #include "tinylu.h"
 #include "tl_handle.h"
 #include "tl_internal.h"
 #include "tl_smem.cuh"
 
 namespace tl {
+
+#if TL_CHECK_BOUNDS
+namespace chk {
+// Readers of the violation words of every checked translation unit.
+static std::vector<Reader> &readers()
+{
+    static std::vector<Reader> v;
+    return v;
+}
+void register_reader(Reader r) { readers().push_back(r); }
+}  // namespace chk
+#endif
 
 // Zero-initialized before any dynamic initializer runs, so the
 // instantiation units may register from their static constructors in any
@@ -257,6 +271,26 @@ tl_status tl_last_cuda_error(tl_handle *h, int *err)
 }
 
 int tl_last_bad_arg(tl_handle *h) { return h ? h->last_bad_arg : 0; }
+
+tl_status tl_check_bounds_violations(unsigned long long *count)
+{
+    if (!count) return TL_ERR_INVALID_ARG;
+    *count = 0;
+#if TL_CHECK_BOUNDS
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return TL_ERR_CUDA;
+    }
+    for (chk::Reader r : chk::readers()) {
+        const unsigned long long v = r();
+        if (v == ~0ULL) return TL_ERR_CUDA;
+        *count += v;
+    }
+    return TL_OK;
+#else
+    return TL_ERR_UNSUPPORTED;
+#endif
+}
 
 tl_status tl_getrf_batched(tl_handle *h, int n, double *A, tl_layout layout, int64_t ld_batch,
                            int32_t *ipiv, int32_t *info, int64_t batch, cudaStream_t stream)

@@ -5,6 +5,7 @@
 // solver family (Sec. 4.1, reporting convention); tl_autotune builds that
 // table by timing every registered variant on the current device, and
 // tl_dispatch_set / tl_dispatch_get read and write it directly.
+#include <algorithm>
 #include <cstdio>
 #include <vector>
 
@@ -100,15 +101,28 @@ extern "C" tl_status tl_autotune(tl_handle *h, int n_min, int n_max, tl_layout l
         return TL_ERR_UNSUPPORTED;
     cudaGetLastError();
 
-    // One tuning batch sized for the largest n: enough systems to fill every
-    // SM several times over with the widest mapping.
-    const int64_t batch = static_cast<int64_t>(h->sm_count) * 512;
-    const int64_t ld = (batch + 31) / 32 * 32;
-    const int64_t nA = static_cast<int64_t>(n_max) * n_max * ld;
-    const int64_t nv = static_cast<int64_t>(n_max) * ld;
+    // Tuning batch per n: about 1.6 GFLOP of algorithmic work (some 2 ms at
+    // the rates these kernels reach), never fewer than 512 systems per SM
+    // nor more than 2^19: the shared-memory variants only show their speed
+    // once every SM holds several waves of their blocks.
+    auto batch_of = [&](int n) {
+        const double fl = 2.0 * ((n - 1.0) * n * (2.0 * n - 1.0) / 6.0 + n * (n - 1.0)) + n * (n - 1.0) / 2.0 + 2.0 * n;
+        int64_t b = static_cast<int64_t>(1.6e9 / fl);
+        const int64_t lo = static_cast<int64_t>(h->sm_count) * 512;
+        b = b < lo ? lo : b;
+        return b > (int64_t(1) << 19) ? (int64_t(1) << 19) : b;
+    };
+    int64_t nA = 0, nv = 0, batch = 0;
+    for (int n = n_min; n <= n_max; ++n) {
+        const int64_t b = batch_of(n), l = (b + 31) / 32 * 32;
+        nA = std::max<int64_t>(nA, static_cast<int64_t>(n) * n * l);
+        nv = std::max<int64_t>(nv, static_cast<int64_t>(n) * l);
+        batch = std::max(batch, b);
+    }
     double *dA = nullptr, *db = nullptr, *dx = nullptr;
     int32_t *dp = nullptr, *di = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStream_t ts = nullptr;  // a private non-blocking stream: nothing else is serialized behind the tuning
     tl_status st = TL_OK;
     struct Row {
         int n, variant, block;
@@ -123,6 +137,10 @@ extern "C" tl_status tl_autotune(tl_handle *h, int n_min, int n_max, tl_layout l
         cudaFree(di);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
+        if (ts) {
+            cudaStreamSynchronize(ts);
+            cudaStreamDestroy(ts);
+        }
     };
     if (cudaMalloc(&dA, nA * sizeof(double)) != cudaSuccess || cudaMalloc(&db, nv * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&dx, nv * sizeof(double)) != cudaSuccess || cudaMalloc(&dp, nv * sizeof(int32_t)) != cudaSuccess ||
@@ -131,13 +149,18 @@ extern "C" tl_status tl_autotune(tl_handle *h, int n_min, int n_max, tl_layout l
         cleanup();
         return TL_ERR_NO_MEMORY;
     }
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    k_fill_uniform<<<h->sm_count * 4, 256>>>(dA, nA, 12345);
-    k_fill_uniform<<<h->sm_count * 4, 256>>>(db, nv, 54321);
+    if (cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        const tl_status fs = fail_cuda(h, cudaGetLastError());
+        cleanup();
+        return fs;
+    }
+    k_fill_uniform<<<h->sm_count * 4, 256, 0, ts>>>(dA, nA, 12345);
+    k_fill_uniform<<<h->sm_count * 4, 256, 0, ts>>>(db, nv, 54321);
 
     for (int n = n_min; n <= n_max && st == TL_OK; ++n) {
-        SolveArgs args{dA, nullptr, db, dx, dp, di, ld, batch, 1};
+        const int64_t bn = batch_of(n), ld = (bn + 31) / 32 * 32;
+        SolveArgs args{dA, nullptr, db, dx, dp, di, ld, bn, 1};
         const VariantList &l = registry(n, layout, kOpGesv);
         float best_ms = 1e30f;
         int best_var = 0, best_block = 0;
@@ -149,9 +172,9 @@ extern "C" tl_status tl_autotune(tl_handle *h, int n_min, int n_max, tl_layout l
                     continue;
                 float ms_best = 1e30f;
                 for (int rep = 0; rep < 3; ++rep) {
-                    cudaEventRecord(e0, nullptr);
-                    st = launch_variant(h, v, n, block, args, nullptr);
-                    cudaEventRecord(e1, nullptr);
+                    cudaEventRecord(e0, ts);
+                    st = launch_variant(h, v, n, block, args, ts);
+                    cudaEventRecord(e1, ts);
                     if (st != TL_OK) break;
                     if (cudaEventSynchronize(e1) != cudaSuccess) {
                         st = fail_cuda(h, cudaGetLastError());
@@ -178,12 +201,14 @@ extern "C" tl_status tl_autotune(tl_handle *h, int n_min, int n_max, tl_layout l
     if (st == TL_OK && table_path) {
         FILE *f = std::fopen(table_path, "w");
         if (!f) return TL_ERR_INVALID_ARG;
-        std::fprintf(f, "{\"layout\": %d, \"batch\": %lld, \"entries\": [", static_cast<int>(layout),
+        std::fprintf(f, "{\"layout\": %d, \"max_batch\": %lld, \"entries\": [", static_cast<int>(layout),
                      static_cast<long long>(batch));
         for (size_t i = 0; i < table.size(); ++i)
-            std::fprintf(f, "%s{\"n\": %d, \"variant\": %d, \"lanes\": %d, \"storage\": \"%s\", \"block\": %d, \"ms\": %.6f}",
+            std::fprintf(f, "%s{\"n\": %d, \"variant\": %d, \"lanes\": %d, \"storage\": \"%s\", \"block\": %d, "
+                            "\"batch\": %lld, \"ms\": %.6f}",
                          i ? ", " : "", table[i].n, table[i].variant, table[i].variant % 100,
-                         table[i].variant >= 100 ? "shared" : "registers", table[i].block, table[i].ms);
+                         table[i].variant >= 100 ? "shared" : "registers", table[i].block,
+                         static_cast<long long>(batch_of(table[i].n)), table[i].ms);
         std::fprintf(f, "]}\n");
         std::fclose(f);
     }

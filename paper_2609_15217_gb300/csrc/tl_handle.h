@@ -51,6 +51,9 @@ tl_status ensure_workspace(tl_handle *h, size_t bytes, cudaStream_t stream);
 tl_status ragged_solve(tl_handle *h, int64_t batch, const int32_t *n, RaggedArgs r, int32_t *ws,
                        cudaStream_t stream, bool mixed = false);
 size_t ragged_ws_ints(int64_t batch, bool mixed);
+// int32 slots in front of the bucket indices in the ragged workspace: bin
+// counts, offsets and cursors (64 each) and the persistent launch's plan.
+constexpr int kRaggedHeaderInts = 4 * 64;
 
 }  // namespace tl
 
@@ -61,6 +64,7 @@ struct tl_handle {
     int max_smem_per_block = 48 * 1024;
     int last_cuda_error = 0;
     int last_bad_arg = 0;
+    int ragged_mode = TL_RAGGED_PERSISTENT;  // tl_ragged_set_mode
     tl::Choice choice[TL_MAX_N + 1][2][tl::kOps] = {};
     std::unordered_map<std::pair<const void *, int>, int, tl::PairHash> occupancy;
     std::unordered_map<const void *, int> smem_opt_in;  // kernel -> dynamic smem limit set

@@ -39,11 +39,13 @@ struct Registrar {
         reg_one_layout<TL_INST_N, TL_INST_T, kPerSystem>();
         reg_one_layout<TL_INST_N, TL_INST_T, kInterleaved>();
         // ragged batches are per-system storage only; registered in slot 0
+        // (register groups only up to n = 16: above, the shared-memory
+        // solvers are faster and the register groups spill)
         if constexpr (TL_INST_T == 1)
             register_variant(TL_INST_N, kPerSystem, kOpRagged, 1,
                              reinterpret_cast<const void *>(&k_ragged_thread<TL_INST_N>), 0,
                              reinterpret_cast<const void *>(&k_ragged_fixup<TL_INST_N>));
-        else
+        else if constexpr (TL_INST_N <= 16)
             register_variant(TL_INST_N, kPerSystem, kOpRagged, TL_INST_T,
                              reinterpret_cast<const void *>(&k_ragged_group<TL_INST_N, TL_INST_T>));
     }

@@ -7,17 +7,17 @@
 namespace tl {
 namespace {
 
-template <int T, int L, bool WALK = (T >= 16)>
+template <int T, int L, bool WALK = (T >= 16), bool ASYNC = true>
 void reg_smem()
 {
-    constexpr int kind = (WALK && T < 16) ? 2 : 1;
+    constexpr int kind = !ASYNC ? 3 : (WALK && T < 16) ? 2 : 1;
     for (int n = 2; n <= TL_MAX_N; ++n) {
-        register_variant(n, L, kOpGesv, T, reinterpret_cast<const void *>(&k_smem_group<T, L, kGesv, false, WALK>),
-                         kind);
-        register_variant(n, L, kOpGesvLU, T, reinterpret_cast<const void *>(&k_smem_group<T, L, kGesv, true, WALK>),
-                         kind);
-        register_variant(n, L, kOpGetrf, T, reinterpret_cast<const void *>(&k_smem_group<T, L, kGetrf, true, WALK>),
-                         kind);
+        register_variant(n, L, kOpGesv, T,
+                         reinterpret_cast<const void *>(&k_smem_group<T, L, kGesv, false, WALK, ASYNC>), kind);
+        register_variant(n, L, kOpGesvLU, T,
+                         reinterpret_cast<const void *>(&k_smem_group<T, L, kGesv, true, WALK, ASYNC>), kind);
+        register_variant(n, L, kOpGetrf, T,
+                         reinterpret_cast<const void *>(&k_smem_group<T, L, kGetrf, true, WALK, ASYNC>), kind);
     }
 }
 
@@ -47,6 +47,10 @@ struct SmemRegistrar {
         reg_smem<2, kInterleaved, true>();
         reg_smem<4, kInterleaved, true>();
         reg_smem<8, kInterleaved, true>();
+        reg_smem<16, kInterleaved, true, false>();
+        reg_smem<32, kInterleaved, true, false>();
+        reg_smem_ragged<2>();
+        reg_smem_ragged<4>();
         reg_smem_ragged<8>();
         reg_smem_ragged<16>();
         reg_smem_ragged<32>();

@@ -38,6 +38,27 @@ __device__ __forceinline__ double ld_stream(const double *p) { return __ldcs(p);
 __device__ __forceinline__ void st_stream(double *p, double v) { __stcs(p, v); }
 __device__ __forceinline__ void st_stream(int32_t *p, int32_t v) { __stcs(p, v); }
 
+// Asynchronous 8-byte global -> shared copy (cp.async, no register staging):
+// every copy a thread issues is in flight at once, where a load-then-store
+// loop waits for each element's memory latency in turn.
+__device__ __forceinline__ void cp_async8(double *smem_dst, const double *gsrc)
+{
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+
+// Wait for every cp.async the calling thread issued (the caller then
+// synchronizes the threads that read the data).
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;\n" ::: "memory");
+}
+
+// ceil(2^20 / c): floor(x / c) == (x * magic20(c)) >> 20 for 0 <= x < 1024
+// and 1 <= c <= 32 (the error x (m - 2^20/c) / 2^20 stays below 1/c).
+__host__ __device__ constexpr unsigned magic20(int c) { return (1048576u + static_cast<unsigned>(c) - 1u) / c; }
+__device__ __forceinline__ int div20(int x, unsigned m) { return static_cast<int>((static_cast<unsigned>(x) * m) >> 20); }
+
 // ---------------------------------------------------------------------------
 // One thread per system.
 // MODE: kGesv (A const, LU_out optional via KEEP), kGetrf (A in place).

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(128) k_newton_tanh_smem(NewtonBatch B, int n)
             st = newton_decide<32>(r, r0, k, B.rtol, B.max_iter);
             if (st >= 0) break;                        // warp-uniform: r is the same on every lane
             __syncwarp();
-            const int info = smem_lupp<32, true>(M, n, RS, lane, 0, 0.0);
+            const int info = smem_lupp2<32, true, false>(M, n, RS, lane, 0, 0.0);
             if (info != 0) {
                 st = TL_NEWTON_SINGULAR;
                 break;

@@ -24,9 +24,10 @@
 namespace tl {
 namespace {
 
-// 3 x 64 per-size counters, then one int32 system index per system.
+// The ragged workspace header (per-size counters and the plan of the
+// persistent launch), then one int32 system index per system.
 constexpr int64_t kNoAllocMaxBatch = TL_NOALLOC_MAX_BATCH;
-constexpr size_t kScratchInts = 3 * 64 + static_cast<size_t>(kNoAllocMaxBatch);
+constexpr size_t kScratchInts = kRaggedHeaderInts + static_cast<size_t>(kNoAllocMaxBatch);
 
 static __device__ __align__(256) int32_t g_ragged_scratch[kScratchInts];
 

@@ -3,15 +3,20 @@
 //
 // The systems are bucketed by n on the device (histogram, exclusive scan,
 // block-aggregated scatter of the system indices into the handle's
-// workspace), then one persistent grid-stride launch per n solves its bucket
-// with the same per-n kernels as tl_gesv_batched.  No host synchronization:
-// the bucket sizes stay on the device and every launch reads them there.
+// workspace), then ONE persistent launch solves every size class
+// (tl_persist.cuh: work items laid out largest n first, taken by warps from
+// a device counter).  The previous design -- one persistent grid-stride
+// launch per n with the per-n kernels of tl_gesv_batched -- stays available
+// as a mode (tl_ragged_set_mode), the comparator of the single launch.  No
+// host synchronization: the bucket sizes stay on the device and every
+// launch reads them there.
 #include <climits>
 
 #include "tinylu.h"
 #include "tl_handle.h"
 #include "tl_internal.h"
 #include "tl_ir_smem.cuh"
+#include "tl_persist.cuh"
 #include "tl_smem.cuh"
 
 namespace tl {
@@ -107,7 +112,36 @@ tl_status ensure_workspace(tl_handle *h, size_t bytes, cudaStream_t stream)
 
 size_t ragged_ws_ints(int64_t batch, bool mixed)
 {
-    return 3 * kSlots + static_cast<size_t>(batch) + (mixed ? kSlots + static_cast<size_t>(batch) : 0);
+    return kRaggedHeaderInts + static_cast<size_t>(batch) + (mixed ? kSlots + static_cast<size_t>(batch) : 0);
+}
+
+// Lanes per system of the single persistent launch for size n when the
+// dispatch table names no shared-memory ragged variant: the fastest
+// element-walk variants measured on GB300 (4 lanes up to n = 10, 8 up to
+// 16, 16 up to 22, a warp above), within a per-warp shared-memory slice of
+// 4 x 296 doubles (the 8-lane need at n = 16; 16 lanes at n = 23, 24 would
+// need more, so a warp takes those).
+int default_persist_lanes(int n)
+{
+    if (n <= 10) return 4;
+    if (n <= 16) return 8;
+    if (n <= 22) return 16;
+    return 32;
+}
+
+// Lanes per system of the single launch for n: the dispatch table's
+// shared-memory ragged variant, else the default; widened until one warp's
+// systems fit in `limit` bytes of shared memory.
+int persist_lanes(const tl_handle *h, int n, int limit)
+{
+    int T = default_persist_lanes(n);
+    const int id = h->choice[n][kPerSystem][kOpRagged].lanes;
+    if (id >= 100) {
+        const int L = id % 100;
+        if (L == 2 || L == 4 || L == 8 || L == 16 || L == 32) T = L;
+    }
+    while (T < 32 && static_cast<size_t>(32 / T) * smem_sys_bytes(n, T) > static_cast<size_t>(limit)) T *= 2;
+    return T;
 }
 
 namespace {
@@ -153,8 +187,42 @@ tl_status launch_smem_ragged(tl_handle *h, const Variant *v, int nn, int64_t bat
     return TL_ERR_UNSUPPORTED;
 }
 
-// Binary64 ragged kernels for every n over the lists in r.
-tl_status launch_binary64(tl_handle *h, int64_t batch, RaggedArgs &r, cudaStream_t stream)
+// The single persistent launch (plus its one-thread planning kernel) over
+// the lists in r.
+tl_status launch_persist(tl_handle *h, RaggedArgs &r, int32_t *plan, cudaStream_t stream)
+{
+    const void *kern = reinterpret_cast<const void *>(&k_ragged_persist);
+    int limit = 0;
+    const tl_status st = smem_opt_in(h, kern, &limit);
+    if (st != TL_OK) return st;
+    PersistPlan P{};
+    int need = 0;
+    P.lanes[0] = 32;
+    for (int n = 1; n <= TL_MAX_N; ++n) {
+        const int T = persist_lanes(h, n, limit);
+        P.lanes[n] = static_cast<unsigned char>(T);
+        const int w = (32 / T) * smem_sys_doubles(n, T);
+        need = w > need ? w : need;
+    }
+    P.warp_doubles = need;
+    P.plan = plan;
+    k_ragged_plan<<<1, 32, 0, stream>>>(r, P);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    const size_t smem = static_cast<size_t>(need) * sizeof(double);
+    if (smem > static_cast<size_t>(limit)) return TL_ERR_UNSUPPORTED;
+    const int nb = blocks_per_sm(h, kern, 32, smem);
+    if (nb < 1) return TL_ERR_UNSUPPORTED;
+    const unsigned grid = static_cast<unsigned>(nb * h->sm_count);
+    void *params[] = {&r, &P};
+    e = cudaLaunchKernel(kern, dim3(grid), dim3(32), params, smem, stream);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    return TL_OK;
+}
+
+// Binary64 ragged kernels for every n over the lists in r (one launch per
+// size class, the per-size mode).
+tl_status launch_per_size(tl_handle *h, RaggedArgs &r, cudaStream_t stream, int64_t batch)
 {
     for (int nn = 1; nn <= TL_MAX_N; ++nn) {
         const Choice &c = h->choice[nn][kPerSystem][kOpRagged];
@@ -175,10 +243,17 @@ tl_status launch_binary64(tl_handle *h, int64_t batch, RaggedArgs &r, cudaStream
     return TL_OK;
 }
 
+tl_status launch_binary64(tl_handle *h, int64_t batch, RaggedArgs &r, int32_t *plan, cudaStream_t stream)
+{
+    if (h->ragged_mode == TL_RAGGED_PER_SIZE) return launch_per_size(h, r, stream, batch);
+    return launch_persist(h, r, plan, stream);
+}
+
 }  // namespace
 
-// Bucket the batch by size and launch every per-n ragged kernel.  `ws` holds
-// 3 * kSlots int32 bin arrays followed by `batch` int32 indices, and with
+// Bucket the batch by size and solve every size class.  `ws` holds the
+// kRaggedHeaderInts int32 header (bin counts, offsets, cursors, the
+// persistent launch's plan) followed by `batch` int32 indices, and with
 // mixed precision kSlots fallback counters and `batch` fallback indices.
 tl_status ragged_solve(tl_handle *h, int64_t batch, const int32_t *n, RaggedArgs r, int32_t *ws,
                        cudaStream_t stream, bool mixed)
@@ -186,7 +261,8 @@ tl_status ragged_solve(tl_handle *h, int64_t batch, const int32_t *n, RaggedArgs
     int32_t *counts = ws;
     int32_t *offsets = ws + kSlots;
     int32_t *cursor = ws + 2 * kSlots;
-    int32_t *bucket = ws + 3 * kSlots;
+    int32_t *plan = ws + 3 * kSlots;
+    int32_t *bucket = ws + kRaggedHeaderInts;
     cudaError_t e = cudaMemsetAsync(counts, 0, kSlots * sizeof(int32_t), stream);
     if (e == cudaSuccess && mixed) e = cudaMemsetAsync(bucket + batch, 0, kSlots * sizeof(int32_t), stream);
     if (e != cudaSuccess) return fail_cuda(h, e);
@@ -199,7 +275,7 @@ tl_status ragged_solve(tl_handle *h, int64_t batch, const int32_t *n, RaggedArgs
     r.bucket = bucket;
     r.offsets = offsets;
     r.counts = nullptr;
-    if (!mixed) return launch_binary64(h, batch, r, stream);
+    if (!mixed) return launch_binary64(h, batch, r, plan, stream);
 
     // mixed precision: binary32 factor + binary64 refinement for every n,
     // then the binary64 kernels over the systems each size handed back
@@ -224,7 +300,7 @@ tl_status ragged_solve(tl_handle *h, int64_t batch, const int32_t *n, RaggedArgs
     RaggedArgs fb = r;
     fb.bucket = r.fb_list;
     fb.counts = r.fb_count;
-    return launch_binary64(h, batch, fb, stream);
+    return launch_binary64(h, batch, fb, plan, stream);
 }
 
 }  // namespace tl
@@ -260,4 +336,13 @@ extern "C" tl_status tl_lupp_solve_batched(tl_handle *h, int64_t batch, const in
     RaggedArgs r{nullptr, nullptr, a_off, A, b_off, b, x, piv_off, ipiv, info};
     r.refine = mixed ? refine_steps : nullptr;
     return ragged_solve(h, batch, n, r, static_cast<int32_t *>(h->ws), stream, mixed);
+}
+
+extern "C" tl_status tl_ragged_set_mode(tl_handle *h, int mode)
+{
+    if (!h) return TL_ERR_INVALID_ARG;
+    h->last_bad_arg = 0;
+    if (mode != TL_RAGGED_PERSISTENT && mode != TL_RAGGED_PER_SIZE) return fail_arg(h, 2);
+    h->ragged_mode = mode;
+    return TL_OK;
 }

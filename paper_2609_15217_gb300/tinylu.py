@@ -22,6 +22,7 @@ _lib = C.CDLL(LIB_PATH)
 TL_OK, TL_ERR_INVALID_ARG, TL_ERR_CUDA, TL_ERR_NO_MEMORY, TL_ERR_UNSUPPORTED, TL_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 TL_LAYOUT_PER_SYSTEM, TL_LAYOUT_INTERLEAVED = 0, 1
 TL_PREC_FP64, TL_PREC_FP32_IR = 0, 1
+TL_RAGGED_PERSISTENT, TL_RAGGED_PER_SIZE = 0, 1
 TL_LAW_NORTON, TL_LAW_TANH = 0, 1
 TL_NEWTON_CONVERGED, TL_NEWTON_MAX_ITER, TL_NEWTON_SINGULAR, TL_NEWTON_NONFINITE = 0, 1, 2, 3
 TL_MAX_N = 32
@@ -80,6 +81,8 @@ _SIGS = {
     "tl_server_pause": ([_vp, _int], _int),
     "tl_server_destroy": ([_vp], _int),
     "tl_dispatch_set": ([_vp, _int, _int, _int, _int], _int),
+    "tl_ragged_set_mode": ([_vp, _int], _int),
+    "tl_check_bounds_violations": ([C.POINTER(C.c_ulonglong)], _int),
     "tl_measure_fma_peak": ([_vp, _int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double), _vp],
                             _int),
     "tl_dispatch_get": ([_vp, _int, _int, C.POINTER(_int), C.POINTER(_int)], _int),
@@ -222,6 +225,18 @@ def tl_gesv_batched_tilepiv(h, n, tile, threshold, A, LU_out, b, x, ipiv, info, 
 
 def tl_autotune(h, n_min, n_max, layout, table_path=None):
     return _lib.tl_autotune(h, n_min, n_max, layout, table_path.encode() if table_path else None)
+
+
+def tl_check_bounds_violations():
+    """Returns (status, violations); TL_ERR_UNSUPPORTED in this (unchecked)
+    library -- libtinylu_checked.so carries the checks."""
+    v = C.c_ulonglong(0)
+    st = _lib.tl_check_bounds_violations(C.byref(v))
+    return st, v.value
+
+
+def tl_ragged_set_mode(h, mode):
+    return _lib.tl_ragged_set_mode(h, mode)
 
 
 def tl_dispatch_set(h, n, layout, variant, block=0):

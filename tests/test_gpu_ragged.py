@@ -59,7 +59,7 @@ def make_ragged(sizes, seed, gap=3):
     return systems, a_off, b_off, p_off, Abuf, bbuf, pp + 1
 
 
-def run_ragged(tl, h, sizes, a_off, b_off, p_off, Abuf, bbuf, npiv):
+def run_ragged(tl, h, sizes, a_off, b_off, p_off, Abuf, bbuf, npiv, mode=None):
     batch = len(sizes)
     d = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(device=DEV, dtype=dt)  # noqa: E731
     dn = d(sizes.astype(np.int32), torch.int32)
@@ -68,7 +68,12 @@ def run_ragged(tl, h, sizes, a_off, b_off, p_off, Abuf, bbuf, npiv):
     dx = torch.full_like(dbv, -5.0)
     dpiv = torch.full((npiv,), -5, dtype=torch.int32, device=DEV)
     dinfo = torch.full((batch,), -5, dtype=torch.int32, device=DEV)
-    st = tl.tl_lupp_solve_batched(h, batch, dn, da, dA, db, dbv, dx, dp, dpiv, dinfo)
+    if mode is not None:
+        assert tl.tl_ragged_set_mode(h, mode) == tl.TL_OK
+    try:
+        st = tl.tl_lupp_solve_batched(h, batch, dn, da, dA, db, dbv, dx, dp, dpiv, dinfo)
+    finally:
+        tl.tl_ragged_set_mode(h, tl.TL_RAGGED_PERSISTENT)
     tl.check("tl_lupp_solve_batched", st, h)
     torch.cuda.synchronize()
     return dx.cpu().numpy(), dpiv.cpu().numpy(), dinfo.cpu().numpy()
@@ -129,3 +134,61 @@ def test_ragged_argument_errors(tl, h):
     assert tl.tl_lupp_solve_batched(h, 4, i32, i64, None, i64, d, d, i64, i32, i32) == tl.TL_ERR_INVALID_ARG
     assert tl.tl_last_bad_arg(h) == 5
     assert tl.tl_lupp_solve_batched(h, 4, i32, i64, d, i64, d, d, i64, i32, i32, prec=7) == tl.TL_ERR_INVALID_ARG
+
+
+def plant_special(systems, Abuf, bbuf, a_off):
+    """A zero column and a NaN entry in a few systems of each size (the
+    oracle copy is updated too)."""
+    for n, (idx, A, b) in systems.items():
+        for q, kind in ((0, "zero"), (1, "nan")):
+            if q >= len(idx) or n < 2:
+                continue
+            s = idx[q]
+            if kind == "zero":
+                A[q, :, n // 2] = 0.0
+            else:
+                A[q, n - 1, 0] = np.nan
+            Abuf[a_off[s]:a_off[s] + n * n] = A[q].T.reshape(-1)
+
+
+def test_persistent_launch_equals_per_size_launches(tl, h):
+    # one persistent launch over every size class against one launch per
+    # size: identical x, pivots and info, bit for bit
+    g = inputs.rng(84)
+    sizes = g.integers(1, 33, size=4000).astype(np.int64)
+    sizes[g.choice(4000, size=8, replace=False)] = 0
+    systems, a_off, b_off, p_off, Abuf, bbuf, npiv = make_ragged(sizes, 85)
+    plant_special(systems, Abuf, bbuf, a_off)
+    xp, pp, ip = run_ragged(tl, h, sizes, a_off, b_off, p_off, Abuf, bbuf, npiv, tl.TL_RAGGED_PERSISTENT)
+    xs, ps, is_ = run_ragged(tl, h, sizes, a_off, b_off, p_off, Abuf, bbuf, npiv, tl.TL_RAGGED_PER_SIZE)
+    assert np.array_equal(ip, is_) and np.array_equal(pp, ps)
+    assert np.array_equal(xp.view(np.int64), xs.view(np.int64))
+    for n, (idx, A, b) in systems.items():
+        _, pivo, infoo, _ = oracle.gesv(A, b)
+        assert np.array_equal(ip[idx], infoo), n
+        assert np.array_equal(np.stack([pp[p_off[s]:p_off[s] + n] for s in idx]), pivo), n
+
+
+@pytest.mark.parametrize("lanes", [2, 4, 8, 16, 32])
+def test_persistent_launch_every_lane_count(tl, h, lanes):
+    # the dispatch table's shared-memory ragged variant sets the lanes per
+    # system of each size in the single launch
+    for n in range(2, 33):
+        assert tl.tl_dispatch_set(h, n, tl.TL_LAYOUT_PER_SYSTEM, tl.variant_id(lanes, shared=True), 0) == tl.TL_OK
+    try:
+        g = inputs.rng(86 + lanes)
+        sizes = g.integers(1, 33, size=1500).astype(np.int64)
+        systems, a_off, b_off, p_off, Abuf, bbuf, npiv = make_ragged(sizes, 87 + lanes)
+        x, piv, info = run_ragged(tl, h, sizes, a_off, b_off, p_off, Abuf, bbuf, npiv)
+        check_ragged(sizes, systems, b_off, p_off, x, piv, info)
+    finally:
+        for n in range(2, 33):
+            tl.tl_dispatch_set(h, n, tl.TL_LAYOUT_PER_SYSTEM, 0, 0)
+
+
+def test_ragged_one_size_only(tl, h):
+    for n in (1, 5, 32):
+        sizes = np.full(700, n, np.int64)
+        systems, a_off, b_off, p_off, Abuf, bbuf, npiv = make_ragged(sizes, 200 + n)
+        x, piv, info = run_ragged(tl, h, sizes, a_off, b_off, p_off, Abuf, bbuf, npiv)
+        check_ragged(sizes, systems, b_off, p_off, x, piv, info)
