@@ -220,13 +220,37 @@ def time_sweep(tl, h, data, layout, steps, warmup, torch, dist_barrier):
     return step_ms, per_n
 
 
-def sweep_e2e(tl, h, n_list, layout, steps, warmup, torch, device, L):
+def host_link_gbs(torch, device, nbytes=1 << 32, reps=3):
+    """Pinned host <-> device copy bandwidth of this machine (GB/s, best of
+    `reps` copies of `nbytes` each way), the reference the end-to-end rate
+    is read against."""
+    hbuf = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    dbuf = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    out = {}
+    for name, (dst, src) in (("h2d", (dbuf, hbuf)), ("d2h", (hbuf, dbuf))):
+        best = 1e30
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            dst.copy_(src, non_blocking=True)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out[name] = nbytes / (best / 1e3) / 1e9
+    del hbuf, dbuf
+    return out
+
+
+def sweep_e2e(tl, h, n_list, layout, steps, warmup, torch, device, L, I, seed):
     """Same sweep through host buffers: every step copies each n's A and b
     from pinned host memory, solves, and copies x, ipiv and info back.  One
-    pinned pool (sized for the largest n, U[-1,1] entries) backs every n's
-    inputs.  The copies and solves are pipelined over the sizes: copy-in,
-    solve and copy-out run on their own streams with two device buffer sets,
-    so the next size's inputs cross the link while the current size solves."""
+    pinned pool backs every n's inputs: the sweep recipe's batch of the
+    largest n (half U[-1,1], half kappa-controlled), in the layout; smaller n
+    read its leading entries.  The copies and solves are pipelined over the
+    sizes: copy-in, solve and copy-out run on their own streams with two
+    device buffer sets, so the next size's inputs cross the link while the
+    current size solves."""
     sizes = {}
     h2d = d2h = 0
     for n in n_list:
@@ -239,10 +263,15 @@ def sweep_e2e(tl, h, n_list, layout, steps, warmup, torch, device, L):
     bigA = max(v[2] for v in sizes.values())
     bigv = max(v[3] for v in sizes.values())
     bigS = max(v[0] for v in sizes.values())
-    g = torch.Generator()
-    g.manual_seed(9001)
-    hA = torch.empty(bigA, dtype=torch.float64).uniform_(-1.0, 1.0, generator=g).pin_memory()
-    hb = torch.empty(bigv, dtype=torch.float64).uniform_(-1.0, 1.0, generator=g).pin_memory()
+    n_pool = max(n_list, key=lambda n: sizes[n][2])
+    S, ld = sizes[n_pool][0], sizes[n_pool][1]
+    A, b, _x = I.sweep_systems_torch(n_pool, S, seed, device)
+    hA = torch.empty(bigA, dtype=torch.float64).pin_memory()
+    hb = torch.empty(bigv, dtype=torch.float64).pin_memory()
+    hA[:sizes[n_pool][2]].copy_(L.matrices_to_layout(A, layout, ld).reshape(-1)[:sizes[n_pool][2]])
+    hb[:sizes[n_pool][3]].copy_(L.vectors_to_layout(b, layout, ld).reshape(-1)[:sizes[n_pool][3]])
+    del A, b, _x
+    torch.cuda.empty_cache()
     hx = [torch.empty(bigv, dtype=torch.float64).pin_memory() for _ in range(2)]
     hp = [torch.empty(bigv, dtype=torch.int32).pin_memory() for _ in range(2)]
     hi = [torch.empty(bigS, dtype=torch.int32).pin_memory() for _ in range(2)]
@@ -303,10 +332,13 @@ def sweep_e2e(tl, h, n_list, layout, steps, warmup, torch, device, L):
         ms.append(t0.elapsed_time(t1))
     total = sum(v[0] for v in sizes.values())
     med = statistics.median(ms)
+    link = host_link_gbs(torch, device)
     return {"value": total / (med / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": med, "h2d_gb_per_s": h2d / (med / 1e3) / 1e9,
-            "inputs": "one pinned host pool of U[-1,1] entries (sized for the largest n) backs every n's A and b; "
-                      "copy-in, solve and copy-out pipelined over the sizes on three streams"}
+            "host_link_gb_per_s": link, "h2d_frac_of_link": h2d / (med / 1e3) / 1e9 / link["h2d"],
+            "inputs": f"one pinned host pool: the sweep batch of n={n_pool} (half U[-1,1], half kappa in [1e2,1e8], "
+                      "b = A x_true) in the layout, whose leading entries back every n's A and b; copy-in, solve "
+                      "and copy-out pipelined over the sizes on three streams"}
 
 
 # FP64 flops of one Norton law evaluation with its Jacobian and the residual
@@ -516,7 +548,21 @@ def ragged_bench(tl, h, steps, warmup, torch, device, I, seed, batch=RAGGED_BATC
                                     "launches": f"{len(per_n)} tl_gesv_batched (+ fixup passes)",
                                     "pivots_equal_persistent": same,
                                     "inputs": "pre-bucketed contiguous per-n copies (bucketing not timed)"}
+
+    # the same launches fed from the mixed layout: the gather of each size's
+    # A and b into contiguous per-n arrays (index_select, known indices) is
+    # part of the timed region, as a caller holding a mixed batch would pay
+    def run_gather_plain():
+        for n, (idx, ia, ib) in d["buckets"].items():
+            q = per_n[n]
+            torch.index_select(d["A"], 0, ia, out=q["A"])
+            torch.index_select(d["b"], 0, ib, out=q["b"])
+        run_plain()
+    med_g = timed(run_gather_plain)
+    out["fp64_plain_per_n_gesv_with_gather"] = {"ms": med_g, "solves_per_s": batch / (med_g / 1e3),
+                                                "launches": f"{2 * len(per_n)} gathers + {len(per_n)} tl_gesv_batched"}
     out["persistent_vs_plain_per_n"] = out["fp64_plain_per_n_gesv"]["ms"] / out["fp64"]["ms"]
+    out["persistent_vs_plain_per_n_with_gather"] = med_g / out["fp64"]["ms"]
     out["persistent_vs_per_size_launches"] = out["fp64_per_size_launches"]["ms"] / out["fp64"]["ms"]
     out["fp32_ir_speedup"] = out["fp64"]["ms"] / out["fp32_ir"]["ms"]
     del d, per_n
@@ -643,6 +689,10 @@ def serve_bench(tl, h, torch, I, seed, burst=160, seconds=3.0):
         out[mode]["capacity_points_per_s"] = pts / span
         out[mode]["capacity_requests_per_s"] = burst / span
         out[mode]["ticks_in_burst"] = stats["ticks"]
+        # where the burst's time went: the union of the server's kernel
+        # intervals (CUDA events) and the request loop's host time per tick
+        out[mode]["device_busy_fraction"] = stats["kernel_busy_s"] / span
+        out[mode]["host_enqueue_ms_per_tick"] = stats["host_enqueue_s"] / max(1, stats["ticks"]) * 1e3
     cap_rps = out["batched"]["capacity_requests_per_s"]
     mean_pts = pts / burst
     for load in (0.5, 0.8, 0.95):
@@ -810,6 +860,15 @@ def main():
             tl.check("tl_autotune", tl.tl_autotune(h, args.nmin, args.nmax, layout, path), h)
             with open(path) as f:
                 tune[layout] = {e["n"]: e["variant"] for e in json.load(f)["entries"]}
+    if not args.no_autotune and not args.no_ragged:
+        # lanes per system of the persistent ragged launch and the
+        # mixed-precision route, per n
+        log("autotune ragged")
+        path = os.path.join(ROOT, "_build/autotune_ragged.json")
+        tl.check("tl_autotune_ragged", tl.tl_autotune_ragged(h, 1, 32, path), h)
+        with open(path) as f:
+            tune["ragged"] = {e["n"]: {"lanes": e["lanes"], "mixed_refines": e["mixed_refines"]}
+                              for e in json.load(f)["entries"]}
     t_gen = time.perf_counter()
     data = make_sweep(n_list, 1, rank_seed(1236, rank), device, torch, L, I, args.batch)
     gen_s = time.perf_counter() - t_gen
@@ -920,7 +979,8 @@ def main():
     e2e = None
     if not args.no_e2e:
         log("end-to-end sweep")
-        e2e = sweep_e2e(tl, h, n_list, 1, max(2, args.steps // 2), 1, torch, device, L)
+        e2e = sweep_e2e(tl, h, n_list, 1, max(2, args.steps // 2), 1, torch, device, L, I,
+                        rank_seed(1240, rank) * 1000 + args.nmax)
         e2e["value"] *= world
         torch.cuda.empty_cache()
 

@@ -210,10 +210,13 @@ tl_status tl_gesv_batched_tilepiv(tl_handle *h, int n, int tile, double threshol
  *           has not met the test after 3 corrections is solved by the
  *           binary64 LUpp instead (x, ipiv and info exactly as with
  *           TL_PREC_FP64).
+ *           Sizes routed to binary64 (tl_ragged_dispatch_set; by default
+ *           n <= 20, where refinement measured slower) are solved by the
+ *           binary64 LUpp directly.
  *   refine_steps  nullable device int32[batch], TL_PREC_FP32_IR only (not
  *           written with TL_PREC_FP64): corrections applied (0..3), or -1
- *           when the system was solved in binary64 (fallback or n[s]
- *           invalid).
+ *           when the system was solved in binary64 (fallback, size routed
+ *           to binary64, or n[s] invalid).
  * info[s] = -2 when n[s] is outside 1..32 (that system is skipped, its x
  * and ipiv are not written); otherwise as for tl_gesv_batched.
  * Systems are bucketed by n on the device in the handle's workspace (grown
@@ -266,7 +269,10 @@ tl_status tl_ragged_set_mode(tl_handle *h, int mode);
  *   on every GPU that loads the library, from load until process exit.
  *   The first call with a given device current looks up the array's device
  *   address (cudaGetSymbolAddress) and caches it; make that first call
- *   before any stream capture on that device.
+ *   before any stream capture on that device.  The cached address belongs
+ *   to that device's context: after cudaDeviceReset (or anything else that
+ *   destroys the primary context) the library must be unloaded and loaded
+ *   again before this entry is called on that device.
  *   Every call on a device shares the one array and its counters are
  *   cleared at the start of each call on `stream`: calls that may overlap on
  *   the GPU (different streams, or different host threads) race and must be
@@ -369,6 +375,34 @@ tl_status tl_autotune(tl_handle *h, int n_min, int n_max, tl_layout layout,
  */
 tl_status tl_measure_fma_peak(tl_handle *h, int bits, double *tflops, double *fma_per_clk_per_sm,
                               double *sm_mhz, cudaStream_t stream);
+
+/*
+ * tl_autotune_ragged -- tune tl_lupp_solve_batched per size n in
+ * [n_min, n_max] on homogeneous batches of the current device (uniform
+ * [-1, 1] entries, some 1.6 GFLOP of work per size): the lanes per system
+ * of the single persistent binary64 launch (2, 4, 8, 16 or 32; n >= 2) and,
+ * for TL_PREC_FP32_IR, whether size n refines a binary32 factorization or
+ * goes straight to the binary64 solve (whichever was faster; systems whose
+ * conditioning defeats the refinement fall back to binary64 either way, so
+ * workloads with many such systems may prefer binary64 for more sizes).
+ * The choices stay in the handle; table_path (nullable) receives them as
+ * JSON.  Allocates and frees a temporary device batch; synchronizes; must
+ * not run during stream capture.
+ */
+tl_status tl_autotune_ragged(tl_handle *h, int n_min, int n_max, const char *table_path);
+
+/*
+ * tl_ragged_dispatch_set / tl_ragged_dispatch_get -- per size n: lanes per
+ * system of the persistent ragged launch (0 = default: one thread with the
+ * system in registers up to n = 7, then 2 lanes at n = 8, 4 up to 14, 8 up
+ * to 22, 16 above; 1 (n <= 7 only) or 2..32 a power of two) and the
+ * mixed-precision route (-1 = default: refine from n = 21 on, binary64
+ * below; 0 = refine; 1 = binary64; systems of a size routed to binary64 get
+ * refine_steps -1).  get returns the lanes the launch uses (widened when a
+ * warp's systems would not fit in shared memory) and whether n refines.
+ */
+tl_status tl_ragged_dispatch_set(tl_handle *h, int n, int lanes, int mixed_route);
+tl_status tl_ragged_dispatch_get(tl_handle *h, int n, int *lanes, int *refines);
 
 /*
  * tl_dispatch_set / tl_dispatch_get -- read or override the per-n dispatch

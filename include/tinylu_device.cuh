@@ -92,7 +92,11 @@ __device__ __forceinline__ double neg(double x)
 // RN(1/a), IEEE binary64 round to nearest even, computed with integer and
 // FP32 instructions only, so the reciprocal of every elimination step costs
 // no FP64 pipe time (the FP64 pipe is the bottleneck; the integer pipes are
-// mostly idle).  Method: a = X * 2^(e-1075) with the 53-bit integer
+// mostly idle).  The published method followed: Newton-Raphson iteration
+// for the reciprocal from a low-precision seed, then correct rounding by an
+// exact remainder (Markstein, IBM J. Res. Dev. 34(1), 1990; Muller et al.,
+// Handbook of Floating-Point Arithmetic, 2nd ed., 2018, ch. 5), here carried
+// out in integer fixed point.  Method: a = X * 2^(e-1075) with the 53-bit integer
 // significand X; the result significand is Q = RN(2^105 / X):
 //   1. seed  Y0 = RN32(1 / (X >> 29)) * 2^76         (~22 correct bits)
 //   2. two Newton steps in fixed point, Y += Y * (2^105 - X Y) / 2^105

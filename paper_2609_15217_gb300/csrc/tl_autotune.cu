@@ -12,6 +12,7 @@
 #include "tinylu.h"
 #include "tl_handle.h"
 #include "tl_internal.h"
+#include "tl_persist_sizes.h"
 #include "tl_smem.cuh"
 
 namespace tl {
@@ -32,6 +33,31 @@ __global__ void k_fill_uniform(double *p, int64_t count, uint64_t seed)
 }
 
 bool op_takes_variant(int op) { return op == kOpGesv || op == kOpGesvLU || op == kOpGetrf; }
+
+// Tuning batch for size n: about 1.6 GFLOP of algorithmic work (some 2 ms at
+// the rates these kernels reach), never fewer than 512 systems per SM nor
+// more than 2^19: the shared-memory variants only show their speed once
+// every SM holds several waves of their blocks.
+int64_t tuning_batch(const tl_handle *h, int n)
+{
+    const double fl = 2.0 * ((n - 1.0) * n * (2.0 * n - 1.0) / 6.0 + n * (n - 1.0)) + n * (n - 1.0) / 2.0 + 2.0 * n;
+    int64_t b = static_cast<int64_t>(1.6e9 / fl);
+    const int64_t lo = static_cast<int64_t>(h->sm_count) * 512;
+    b = b < lo ? lo : b;
+    return b > (int64_t(1) << 19) ? (int64_t(1) << 19) : b;
+}
+
+// Homogeneous ragged batch for the tuner: every system of size n, stored
+// one after another.
+__global__ void k_ragged_layout(int64_t S, int n, int32_t *nv, int64_t *a_off, int64_t *b_off)
+{
+    for (int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; s < S;
+         s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        nv[s] = n;
+        a_off[s] = s * n * n;
+        b_off[s] = s * n;
+    }
+}
 
 }  // namespace
 }  // namespace tl
@@ -101,17 +127,7 @@ extern "C" tl_status tl_autotune(tl_handle *h, int n_min, int n_max, tl_layout l
         return TL_ERR_UNSUPPORTED;
     cudaGetLastError();
 
-    // Tuning batch per n: about 1.6 GFLOP of algorithmic work (some 2 ms at
-    // the rates these kernels reach), never fewer than 512 systems per SM
-    // nor more than 2^19: the shared-memory variants only show their speed
-    // once every SM holds several waves of their blocks.
-    auto batch_of = [&](int n) {
-        const double fl = 2.0 * ((n - 1.0) * n * (2.0 * n - 1.0) / 6.0 + n * (n - 1.0)) + n * (n - 1.0) / 2.0 + 2.0 * n;
-        int64_t b = static_cast<int64_t>(1.6e9 / fl);
-        const int64_t lo = static_cast<int64_t>(h->sm_count) * 512;
-        b = b < lo ? lo : b;
-        return b > (int64_t(1) << 19) ? (int64_t(1) << 19) : b;
-    };
+    auto batch_of = [&](int n) { return tuning_batch(h, n); };
     int64_t nA = 0, nv = 0, batch = 0;
     for (int n = n_min; n <= n_max; ++n) {
         const int64_t b = batch_of(n), l = (b + 31) / 32 * 32;
@@ -213,4 +229,149 @@ extern "C" tl_status tl_autotune(tl_handle *h, int n_min, int n_max, tl_layout l
         std::fclose(f);
     }
     return st;
+}
+
+extern "C" tl_status tl_autotune_ragged(tl_handle *h, int n_min, int n_max, const char *table_path)
+{
+    if (!h) return TL_ERR_INVALID_ARG;
+    h->last_bad_arg = 0;
+    if (n_min < 1 || n_min > TL_MAX_N) return fail_arg(h, 2);
+    if (n_max < n_min || n_max > TL_MAX_N) return fail_arg(h, 3);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(nullptr, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+        return TL_ERR_UNSUPPORTED;
+    cudaGetLastError();
+    int64_t maxS = 0, maxA = 0, maxV = 0;
+    for (int n = n_min; n <= n_max; ++n) {
+        const int64_t S = tuning_batch(h, n);
+        maxS = std::max(maxS, S);
+        maxA = std::max(maxA, S * n * n);
+        maxV = std::max(maxV, S * n);
+    }
+    double *dA = nullptr, *db = nullptr, *dx = nullptr;
+    int32_t *dp = nullptr, *di = nullptr, *dref = nullptr, *dn = nullptr, *ws = nullptr;
+    int64_t *da = nullptr, *dbo = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStream_t ts = nullptr;
+    auto cleanup = [&]() {
+        if (ts) cudaStreamSynchronize(ts);
+        for (void *p : {static_cast<void *>(dA), static_cast<void *>(db), static_cast<void *>(dx),
+                        static_cast<void *>(dp), static_cast<void *>(di), static_cast<void *>(dref),
+                        static_cast<void *>(dn), static_cast<void *>(ws), static_cast<void *>(da),
+                        static_cast<void *>(dbo)})
+            cudaFree(p);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (ts) cudaStreamDestroy(ts);
+    };
+    if (cudaMalloc(&dA, maxA * 8) != cudaSuccess || cudaMalloc(&db, maxV * 8) != cudaSuccess ||
+        cudaMalloc(&dx, maxV * 8) != cudaSuccess || cudaMalloc(&dp, maxV * 4) != cudaSuccess ||
+        cudaMalloc(&di, maxS * 4) != cudaSuccess || cudaMalloc(&dref, maxS * 4) != cudaSuccess ||
+        cudaMalloc(&dn, maxS * 4) != cudaSuccess || cudaMalloc(&da, maxS * 8) != cudaSuccess ||
+        cudaMalloc(&dbo, maxS * 8) != cudaSuccess ||
+        cudaMalloc(&ws, ragged_ws_ints(maxS, true) * sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return TL_ERR_NO_MEMORY;
+    }
+    if (cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        const tl_status fs = fail_cuda(h, cudaGetLastError());
+        cleanup();
+        return fs;
+    }
+    k_fill_uniform<<<h->sm_count * 4, 256, 0, ts>>>(dA, maxA, 2468);
+    k_fill_uniform<<<h->sm_count * 4, 256, 0, ts>>>(db, maxV, 1357);
+
+    // keep the caller's settings; while a size is tuned every other size
+    // runs with a full warp per system (the smallest shared-memory slice),
+    // so the slice of the launch is the tuned size's own
+    const int mode = h->ragged_mode;
+    h->ragged_mode = TL_RAGGED_PERSISTENT;
+    Choice saved[TL_MAX_N + 1];
+    signed char saved_route[TL_MAX_N + 1];
+    for (int n = 1; n <= TL_MAX_N; ++n) {
+        saved[n] = h->choice[n][kPerSystem][kOpRagged];
+        saved_route[n] = h->mixed_route[n];
+        h->choice[n][kPerSystem][kOpRagged] = Choice{variant_id(n <= kPersistRegMaxN ? 1 : 32, 1), 0};
+    }
+    struct Row {
+        int n, lanes, refine;
+        float ms64, ms_mixed;
+    };
+    std::vector<Row> table;
+    tl_status st = TL_OK;
+    for (int n = n_min; n <= n_max && st == TL_OK; ++n) {
+        const int64_t S = tuning_batch(h, n);
+        k_ragged_layout<<<h->sm_count * 4, 256, 0, ts>>>(S, n, dn, da, dbo);
+        RaggedArgs r{nullptr, nullptr, da, dA, dbo, db, dx, dbo, dp, di};
+        auto time_it = [&](bool mixed, float *out) -> tl_status {
+            RaggedArgs rr = r;
+            rr.refine = mixed ? dref : nullptr;
+            float best = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, ts);
+                const tl_status s2 = ragged_solve(h, S, dn, rr, ws, ts, mixed);
+                cudaEventRecord(e1, ts);
+                if (s2 != TL_OK) return s2;
+                if (cudaEventSynchronize(e1) != cudaSuccess) return fail_cuda(h, cudaGetLastError());
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0 && ms < best) best = ms;  // the first run warms up
+            }
+            *out = best;
+            return TL_OK;
+        };
+        int best_T = 0;
+        float best64 = 1e30f;
+        {
+            for (int T : {1, 2, 4, 8, 16, 32}) {
+                if (T == 1 && n > kPersistRegMaxN) continue;  // one thread in registers up to n = 7
+                // only choices within the launch's slice: a larger one would
+                // shrink the resident warps of every size in a mixed batch
+                if (persist_need(n, T) > kPersistSliceDoubles) continue;
+                h->choice[n][kPerSystem][kOpRagged] = Choice{variant_id(T, 1), 0};
+                float ms = 0.f;
+                if ((st = time_it(false, &ms)) != TL_OK) break;
+                if (ms < best64) {
+                    best64 = ms;
+                    best_T = T;
+                }
+            }
+            if (st != TL_OK) break;
+            h->choice[n][kPerSystem][kOpRagged] = Choice{variant_id(best_T, 1), 0};
+        }
+        h->mixed_route[n] = 0;  // refine
+        float ms_mixed = 0.f;
+        if ((st = time_it(true, &ms_mixed)) != TL_OK) break;
+        h->mixed_route[n] = saved_route[n];
+        // back to the neutral choice while the other sizes are tuned (the
+        // winners are applied together at the end)
+        h->choice[n][kPerSystem][kOpRagged] = Choice{variant_id(n <= kPersistRegMaxN ? 1 : 32, 1), 0};
+        table.push_back(Row{n, best_T, ms_mixed < best64 ? 1 : 0, best64, ms_mixed});
+    }
+    for (int n = 1; n <= TL_MAX_N; ++n) {
+        h->choice[n][kPerSystem][kOpRagged] = saved[n];
+        h->mixed_route[n] = saved_route[n];
+    }
+    h->ragged_mode = mode;
+    cleanup();
+    if (st != TL_OK) return st;
+    for (const Row &row : table) {
+        if (row.lanes) h->choice[row.n][kPerSystem][kOpRagged] = Choice{variant_id(row.lanes, 1), 0};
+        h->mixed_route[row.n] = static_cast<signed char>(row.refine ? 0 : 1);
+    }
+    if (table_path) {
+        FILE *f = std::fopen(table_path, "w");
+        if (!f) return TL_ERR_INVALID_ARG;
+        std::fprintf(f, "{\"entries\": [");
+        for (size_t i = 0; i < table.size(); ++i)
+            std::fprintf(f, "%s{\"n\": %d, \"lanes\": %d, \"mixed_refines\": %d, \"batch\": %lld, "
+                            "\"ms_fp64\": %.6f, \"ms_mixed\": %.6f}",
+                         i ? ", " : "", table[i].n, table[i].lanes, table[i].refine,
+                         static_cast<long long>(tuning_batch(h, table[i].n)), table[i].ms64, table[i].ms_mixed);
+        std::fprintf(f, "]}\n");
+        std::fclose(f);
+    }
+    return TL_OK;
 }

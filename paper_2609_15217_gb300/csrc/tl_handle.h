@@ -50,6 +50,9 @@ tl_status ensure_workspace(tl_handle *h, size_t bytes, cudaStream_t stream);
 // `batch` fallback indices (ragged_ws_ints).
 tl_status ragged_solve(tl_handle *h, int64_t batch, const int32_t *n, RaggedArgs r, int32_t *ws,
                        cudaStream_t stream, bool mixed = false);
+// Mixed precision for size n: true when its systems refine a binary32
+// factorization, false when they go straight to the binary64 solve.
+bool mixed_refines(const tl_handle *h, int n);
 size_t ragged_ws_ints(int64_t batch, bool mixed);
 // int32 slots in front of the bucket indices in the ragged workspace: bin
 // counts, offsets and cursors (64 each) and the persistent launch's plan.
@@ -65,6 +68,9 @@ struct tl_handle {
     int last_cuda_error = 0;
     int last_bad_arg = 0;
     int ragged_mode = TL_RAGGED_PERSISTENT;  // tl_ragged_set_mode
+    // mixed precision per n: -1 default rule, 0 refine, 1 solve in binary64
+    signed char mixed_route[TL_MAX_N + 1] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1,
+                                             -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
     tl::Choice choice[TL_MAX_N + 1][2][tl::kOps] = {};
     std::unordered_map<std::pair<const void *, int>, int, tl::PairHash> occupancy;
     std::unordered_map<const void *, int> smem_opt_in;  // kernel -> dynamic smem limit set

@@ -8,12 +8,14 @@
 // laid out largest n first, so the longest items start first and the short
 // ones fill the tail (longest-processing-time order).  k_ragged_persist is
 // launched with as many one-warp blocks as stay resident; each warp takes
-// the next item from a counter in device memory, loads its systems
+// the next item from a counter in device memory (one item ahead, so the
+// counter's latency overlaps the current item), loads its systems
 // (coalesced, each system is contiguous in memory) into its own slice of
 // shared memory, solves them with the element-walk solver (smem_lupp2) and
 // stores x, the pivots and info.  Size classes without systems have no
 // items; nothing waits on anything (the counter only grows).
 #pragma once
+#include "tl_persist_sizes.h"
 #include "tl_smem.cuh"
 
 namespace tl {
@@ -25,7 +27,7 @@ constexpr int kPlanTotal = TL_MAX_N;
 constexpr int kPlanCounter = 48;
 
 struct PersistPlan {
-    unsigned char lanes[TL_MAX_N + 1];  // lanes per system for each n: 2, 4, 8, 16 or 32
+    unsigned char lanes[TL_MAX_N + 1];  // lanes per system for each n: 1 (n <= 7), 2, 4, 8, 16 or 32
     int warp_doubles;                   // shared-memory slice of one warp
     int32_t *plan;                      // the plan block (device)
 };
@@ -120,8 +122,67 @@ __device__ __forceinline__ void persist_item(const RaggedArgs &r, int n, int64_t
     __syncwarp();  // the next item's loads overwrite the slice
 }
 
-// One warp per block; dynamic shared memory = P.warp_doubles doubles.
-__global__ void __launch_bounds__(32, 24) k_ragged_persist(RaggedArgs r, const __grid_constant__ PersistPlan P)
+// One work item of the one-thread register path (n <= 7): the 32 systems
+// are copied into the warp's slice (coalesced, one system after another),
+// then lane g loads system g into its registers and solves it with the
+// branch-free fast path of the one-thread kernels; a system that meets a
+// zero, tiny, huge or non-finite pivot takes the exact general path.
+template <int N>
+__device__ __forceinline__ void persist_item_reg(const RaggedArgs &r, int64_t beg, int64_t count, int64_t first,
+                                                 double *W, int lane)
+{
+    constexpr int NN = N * N;
+    constexpr int STRIDE = persist_reg_stride(N);
+    const bool act = first + lane < count;
+    int64_t s = 0, ao = 0, bo = 0, po = 0;
+    if (act) {
+        s = r.bucket[beg + first + lane];
+        ao = r.a_off[s];
+        bo = r.b_off[s];
+        po = r.piv_off[s];
+    }
+#pragma unroll 1
+    for (int g = 0; g < 32; ++g) {
+        if (first + g >= count) break;  // warp-uniform
+        const double *A = r.A + __shfl_sync(0xffffffffu, ao, g);
+        const double *bv = r.b + __shfl_sync(0xffffffffu, bo, g);
+        double *M = W + g * STRIDE;
+        for (int e = lane; e < NN; e += 32) cp_async8(&TL_SM(M, e, STRIDE), A + e);
+        if (lane < N) cp_async8(&TL_SM(M, NN + lane, STRIDE), bv + lane);
+    }
+    cp_async_wait_all();
+    __syncwarp();
+    if (act) {
+        const double *M = W + lane * STRIDE;
+        double a[N][N];
+        double b[1][N];
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+#pragma unroll
+            for (int i = 0; i < N; ++i) a[i][j] = TL_SM(M, j * N + i, STRIDE);
+#pragma unroll
+        for (int i = 0; i < N; ++i) b[0][i] = TL_SM(M, NN + i, STRIDE);
+        const bool bad = dev::any_nonfinite<N>(a);
+        int piv[N];
+        double rcp[N];
+        const bool slow = dev::lu_thread_factor_fast<N, false, 1>(a, b, piv, rcp) || bad;
+        if (!slow) {
+            dev::lu_thread_backsolve_fast<N>(a, b[0], rcp);
+#pragma unroll
+            for (int i = 0; i < N; ++i) st_stream(r.x + bo + i, b[0][i]);
+#pragma unroll
+            for (int k = 0; k < N; ++k) st_stream(r.ipiv + po + k, piv[k] + 1);
+            st_stream(r.info + s, 0);
+        } else {
+            slow_ragged_thread<N>(r, s);
+        }
+    }
+    __syncwarp();  // the next item's copies overwrite the slice
+}
+
+// One warp per block; dynamic shared memory = P.warp_doubles doubles.  12
+// blocks per SM (the slice's occupancy) leave 170 registers per thread.
+__global__ void __launch_bounds__(32, 12) k_ragged_persist(RaggedArgs r, const __grid_constant__ PersistPlan P)
 {
     extern __shared__ double smem[];
     __shared__ int32_t s_start[TL_MAX_N + 1];
@@ -134,11 +195,13 @@ __global__ void __launch_bounds__(32, 24) k_ragged_persist(RaggedArgs r, const _
     __syncwarp();
     const int32_t total = s_start[kPlanTotal];
     int c = 0;
-    for (;;) {
-        int32_t item = 0;
-        if (lane == 0) item = atomicAdd(P.plan + kPlanCounter, 1);
-        item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= total) break;
+    int32_t item = 0;
+    if (lane == 0) item = atomicAdd(P.plan + kPlanCounter, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    while (item < total) {
+        // take the next item now: the counter's latency overlaps this item
+        int32_t next = 0;
+        if (lane == 0) next = atomicAdd(P.plan + kPlanCounter, 1);
         while (item >= s_start[c + 1]) ++c;  // items only grow: c never goes back
         const int n = TL_MAX_N - c;
         const int T = s_lanes[n];
@@ -146,12 +209,24 @@ __global__ void __launch_bounds__(32, 24) k_ragged_persist(RaggedArgs r, const _
         const int64_t count = class_count(r, n);
         const int64_t first = static_cast<int64_t>(item - s_start[c]) * (32 / T);
         switch (T) {
+        case 1:
+            switch (n) {
+            case 1: persist_item_reg<1>(r, beg, count, first, smem, lane); break;
+            case 2: persist_item_reg<2>(r, beg, count, first, smem, lane); break;
+            case 3: persist_item_reg<3>(r, beg, count, first, smem, lane); break;
+            case 4: persist_item_reg<4>(r, beg, count, first, smem, lane); break;
+            case 5: persist_item_reg<5>(r, beg, count, first, smem, lane); break;
+            case 6: persist_item_reg<6>(r, beg, count, first, smem, lane); break;
+            default: persist_item_reg<kPersistRegMaxN>(r, beg, count, first, smem, lane); break;
+            }
+            break;
         case 2: persist_item<2>(r, n, beg, count, first, smem, lane); break;
         case 4: persist_item<4>(r, n, beg, count, first, smem, lane); break;
         case 8: persist_item<8>(r, n, beg, count, first, smem, lane); break;
         case 16: persist_item<16>(r, n, beg, count, first, smem, lane); break;
         default: persist_item<32>(r, n, beg, count, first, smem, lane); break;
         }
+        item = __shfl_sync(0xffffffffu, next, 0);
     }
 }
 

@@ -59,6 +59,26 @@ __global__ void k_bucket_scan(const int32_t *__restrict__ counts, int32_t *__res
     }
 }
 
+// Mixed precision, sizes routed to binary64: their bucket entries become
+// their fallback lists as they are (the same positions), their refinement
+// counts -1.  `routed` has bit n set for every routed size.
+__global__ void k_route_binary64(int64_t batch, const int32_t *__restrict__ n, const int32_t *__restrict__ offsets,
+                                 const int32_t *__restrict__ bucket, int32_t *__restrict__ fb_count,
+                                 int32_t *__restrict__ fb_list, int32_t *__restrict__ refine, unsigned long long routed)
+{
+    const int64_t i0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i0 <= TL_MAX_N && i0 >= 1 && ((routed >> i0) & 1ULL))
+        fb_count[i0] = offsets[i0 + 1] - offsets[i0];
+    const int64_t total = offsets[TL_MAX_N + 1];
+    for (int64_t i = i0; i < total; i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int32_t s = bucket[i];
+        if ((routed >> n[s]) & 1ULL) {
+            fb_list[i] = s;
+            if (refine) refine[s] = -1;
+        }
+    }
+}
+
 __global__ void k_bucket_scatter(int64_t batch, const int32_t *__restrict__ n, int32_t *__restrict__ cursor,
                                  int32_t *__restrict__ bucket)
 {
@@ -116,31 +136,42 @@ size_t ragged_ws_ints(int64_t batch, bool mixed)
 }
 
 // Lanes per system of the single persistent launch for size n when the
-// dispatch table names no shared-memory ragged variant: the fastest
-// element-walk variants measured on GB300 (4 lanes up to n = 10, 8 up to
-// 16, 16 up to 22, a warp above), within a per-warp shared-memory slice of
-// 4 x 296 doubles (the 8-lane need at n = 16; 16 lanes at n = 23, 24 would
-// need more, so a warp takes those).
+// dispatch table names none: the fastest choice measured on GB300 within
+// the launch's slice of kPersistSliceDoubles (one thread in registers up
+// to n = 7, then 2, 4, 8 and 16 lanes in shared memory).
 int default_persist_lanes(int n)
 {
-    if (n <= 10) return 4;
-    if (n <= 16) return 8;
-    if (n <= 22) return 16;
-    return 32;
+    if (n <= kPersistRegMaxN) return 1;
+    if (n <= 8) return 2;
+    if (n <= 14) return 4;
+    if (n <= 22) return 8;
+    return 16;
 }
 
 // Lanes per system of the single launch for n: the dispatch table's
 // shared-memory ragged variant, else the default; widened until one warp's
 // systems fit in `limit` bytes of shared memory.
+// Sizes that refine by default under TL_PREC_FP32_IR: measured on GB300,
+// the binary32 factorization with binary64 refinement beats the binary64
+// solve from n = 21 on (1.1x at n = 21, 1.5-1.7x at n = 25..32) and loses
+// below, where the FP64 pipe is not the only limit.
+constexpr int kMixedMinN = 21;
+
+bool mixed_refines(const tl_handle *h, int n)
+{
+    const int v = h->mixed_route[n];
+    return v < 0 ? n >= kMixedMinN : v == 0;
+}
+
 int persist_lanes(const tl_handle *h, int n, int limit)
 {
     int T = default_persist_lanes(n);
     const int id = h->choice[n][kPerSystem][kOpRagged].lanes;
     if (id >= 100) {
         const int L = id % 100;
-        if (L == 2 || L == 4 || L == 8 || L == 16 || L == 32) T = L;
+        if ((L == 1 && n <= kPersistRegMaxN) || L == 2 || L == 4 || L == 8 || L == 16 || L == 32) T = L;
     }
-    while (T < 32 && static_cast<size_t>(32 / T) * smem_sys_bytes(n, T) > static_cast<size_t>(limit)) T *= 2;
+    while (T < 32 && static_cast<size_t>(persist_need(n, T)) * sizeof(double) > static_cast<size_t>(limit)) T *= 2;
     return T;
 }
 
@@ -196,12 +227,12 @@ tl_status launch_persist(tl_handle *h, RaggedArgs &r, int32_t *plan, cudaStream_
     const tl_status st = smem_opt_in(h, kern, &limit);
     if (st != TL_OK) return st;
     PersistPlan P{};
-    int need = 0;
+    int need = kPersistSliceDoubles;
     P.lanes[0] = 32;
     for (int n = 1; n <= TL_MAX_N; ++n) {
         const int T = persist_lanes(h, n, limit);
         P.lanes[n] = static_cast<unsigned char>(T);
-        const int w = (32 / T) * smem_sys_doubles(n, T);
+        const int w = persist_need(n, T);
         need = w > need ? w : need;
     }
     P.warp_doubles = need;
@@ -277,11 +308,21 @@ tl_status ragged_solve(tl_handle *h, int64_t batch, const int32_t *n, RaggedArgs
     r.counts = nullptr;
     if (!mixed) return launch_binary64(h, batch, r, plan, stream);
 
-    // mixed precision: binary32 factor + binary64 refinement for every n,
-    // then the binary64 kernels over the systems each size handed back
+    // mixed precision: binary32 factor + binary64 refinement for the sizes
+    // that refine, then the binary64 launch over the systems each size
+    // handed back and over every system of the sizes routed to binary64
     r.fb_count = bucket + batch;
     r.fb_list = bucket + batch + kSlots;
+    unsigned long long routed = 0;
+    for (int nn = 1; nn <= TL_MAX_N; ++nn)
+        if (!mixed_refines(h, nn)) routed |= 1ULL << nn;
+    if (routed) {
+        k_route_binary64<<<grid < 1024u ? grid : 1024u, block, 0, stream>>>(batch, n, offsets, bucket, r.fb_count,
+                                                                          r.fb_list, r.refine, routed);
+        if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(h, e);
+    }
     for (int nn = 1; nn <= TL_MAX_N; ++nn) {
+        if ((routed >> nn) & 1ULL) continue;
         const Choice &c = h->choice[nn][kPerSystem][kOpRaggedIr];
         const Variant *v =
             find_variant(nn, kPerSystem, kOpRaggedIr, c.lanes ? c.lanes : default_ir_id(nn));
@@ -344,5 +385,32 @@ extern "C" tl_status tl_ragged_set_mode(tl_handle *h, int mode)
     h->last_bad_arg = 0;
     if (mode != TL_RAGGED_PERSISTENT && mode != TL_RAGGED_PER_SIZE) return fail_arg(h, 2);
     h->ragged_mode = mode;
+    return TL_OK;
+}
+
+extern "C" tl_status tl_ragged_dispatch_set(tl_handle *h, int n, int lanes, int mixed_route)
+{
+    if (!h) return TL_ERR_INVALID_ARG;
+    h->last_bad_arg = 0;
+    if (n < 1 || n > TL_MAX_N) return fail_arg(h, 2);
+    if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
+        return fail_arg(h, 3);
+    if (lanes == 1 && n > kPersistRegMaxN) return fail_arg(h, 3);  // one thread in registers: n <= 7
+    if (mixed_route < -1 || mixed_route > 1) return fail_arg(h, 4);
+    h->choice[n][kPerSystem][kOpRagged] = Choice{lanes ? variant_id(lanes, 1) : 0, 0};
+    h->mixed_route[n] = static_cast<signed char>(mixed_route);
+    return TL_OK;
+}
+
+extern "C" tl_status tl_ragged_dispatch_get(tl_handle *h, int n, int *lanes, int *refines)
+{
+    if (!h) return TL_ERR_INVALID_ARG;
+    h->last_bad_arg = 0;
+    if (n < 1 || n > TL_MAX_N) return fail_arg(h, 2);
+    if (!lanes) return fail_arg(h, 3);
+    int limit = h->max_smem_per_block;
+    smem_opt_in(h, reinterpret_cast<const void *>(&k_ragged_persist), &limit);
+    *lanes = persist_lanes(h, n, limit);
+    if (refines) *refines = mixed_refines(h, n) ? 1 : 0;
     return TL_OK;
 }

@@ -99,9 +99,17 @@ size_t tick_scratch_bytes(size_t table, int64_t nsys)
     return table + (nsys > 0 ? up(ragged_ws_ints(nsys, false) * sizeof(int32_t)) : 0) + 4 * Arena::kAlign;
 }
 
+// Each slot runs its ticks on three streams: copies in (s_in), kernels
+// (stream) and copies out (s_out), so that a tick's later classes copy
+// their inputs while its earlier classes compute, and results go home while
+// the next class runs.
 struct Slot {
-    cudaStream_t stream = nullptr;
-    std::vector<cudaEvent_t> evs;  // kMaxGroups events
+    cudaStream_t stream = nullptr;   // kernels
+    cudaStream_t s_in = nullptr;     // host -> device copies
+    cudaStream_t s_out = nullptr;    // device -> host copies
+    std::vector<cudaEvent_t> evs;    // kMaxGroups events: group done (on s_out)
+    std::vector<cudaEvent_t> ev_in;  // kMaxGroups: group inputs on the device (on s_in)
+    std::vector<cudaEvent_t> ev_k;   // kMaxGroups: group kernels done (on stream)
     std::vector<cudaEvent_t> kev;  // 2 * kMaxGroups timing events around each group's kernels
     tl_handle *h = nullptr;  // own handle: the ragged solve's workspace is per handle
     bool busy = false;
@@ -225,7 +233,7 @@ bool tl_server::form_tick(Slot &, std::vector<Req *> &batch, size_t &scratch_off
 // group and the groups issued before it.
 tl_status tl_server::enqueue(Slot &sl, std::vector<Req *> &batch)
 {
-    cudaStream_t st = sl.stream;
+    cudaStream_t st = sl.stream, s_in = sl.s_in, s_out = sl.s_out;
     cudaError_t e = cudaSuccess;
     auto dptr = [&](size_t off) { return base + off; };
     sl.groups.clear();
@@ -246,37 +254,51 @@ tl_status tl_server::enqueue(Slot &sl, std::vector<Req *> &batch)
     auto close_group = [&](std::vector<Req *> &reqs, bool timed) -> tl_status {
         const size_t g = sl.groups.size();
         if (g >= sl.evs.size()) return TL_ERR_UNSUPPORTED;
-        const cudaError_t er = cudaEventRecord(sl.evs[g], st);
+        const cudaError_t er = cudaEventRecord(sl.evs[g], s_out);
         if (er != cudaSuccess) return fail_cuda(sl.h, er);
         sl.groups.push_back(Group{reqs, false, timed});
         return TL_OK;
+    };
+    // the group's inputs are on the device: its kernels may start
+    auto inputs_ready = [&](size_t g) -> cudaError_t {
+        cudaError_t er = cudaEventRecord(sl.ev_in[g], s_in);
+        if (er == cudaSuccess) er = cudaStreamWaitEvent(st, sl.ev_in[g], 0);
+        return er;
+    };
+    // the group's kernels are done: its results may go home
+    auto kernels_done = [&](size_t g) -> cudaError_t {
+        cudaError_t er = cudaEventRecord(sl.ev_k[g], st);
+        if (er == cudaSuccess) er = cudaStreamWaitEvent(s_out, sl.ev_k[g], 0);
+        return er;
     };
     auto copy_in = [&](Req *r) -> cudaError_t {
         const size_t c = static_cast<size_t>(r->d.count);
         if (r->d.kind == TL_REQ_NEWTON) {
             const size_t ld = r->d.ld_in > 0 ? static_cast<size_t>(r->d.ld_in) : c;
-            if (ld == c) return cudaMemcpyAsync(dptr(r->o_in), r->d.in, c * r->fields() * 8, cudaMemcpyHostToDevice, st);
+            if (ld == c)
+                return cudaMemcpyAsync(dptr(r->o_in), r->d.in, c * r->fields() * 8, cudaMemcpyHostToDevice, s_in);
             return cudaMemcpy2DAsync(dptr(r->o_in), c * 8, r->d.in, ld * 8, c * 8, static_cast<size_t>(r->fields()),
-                                     cudaMemcpyHostToDevice, st);
+                                     cudaMemcpyHostToDevice, s_in);
         }
         const size_t n = static_cast<size_t>(r->d.n);
-        cudaError_t er = cudaMemcpyAsync(dptr(r->o_in), r->d.in, c * n * n * 8, cudaMemcpyHostToDevice, st);
-        if (er == cudaSuccess) er = cudaMemcpyAsync(dptr(r->o_x), r->d.rhs, c * n * 8, cudaMemcpyHostToDevice, st);
+        cudaError_t er = cudaMemcpyAsync(dptr(r->o_in), r->d.in, c * n * n * 8, cudaMemcpyHostToDevice, s_in);
+        if (er == cudaSuccess) er = cudaMemcpyAsync(dptr(r->o_x), r->d.rhs, c * n * 8, cudaMemcpyHostToDevice, s_in);
         return er;
     };
     auto copy_out = [&](Req *r) -> cudaError_t {
         const size_t c = static_cast<size_t>(r->d.count);
         cudaError_t er;
         if (r->d.kind == TL_REQ_NEWTON) {
-            er = cudaMemcpyAsync(r->d.x, dptr(r->o_x), c * r->xrows() * 8, cudaMemcpyDeviceToHost, st);
+            er = cudaMemcpyAsync(r->d.x, dptr(r->o_x), c * r->xrows() * 8, cudaMemcpyDeviceToHost, s_out);
             if (er == cudaSuccess && r->has_aux())
-                er = cudaMemcpyAsync(r->d.aux, dptr(r->o_aux), c * 6 * 8, cudaMemcpyDeviceToHost, st);
-            if (er == cudaSuccess) er = cudaMemcpyAsync(r->d.i1, dptr(r->o_i1), c * 4, cudaMemcpyDeviceToHost, st);
-            if (er == cudaSuccess) er = cudaMemcpyAsync(r->d.i2, dptr(r->o_i2), c * 4, cudaMemcpyDeviceToHost, st);
+                er = cudaMemcpyAsync(r->d.aux, dptr(r->o_aux), c * 6 * 8, cudaMemcpyDeviceToHost, s_out);
+            if (er == cudaSuccess) er = cudaMemcpyAsync(r->d.i1, dptr(r->o_i1), c * 4, cudaMemcpyDeviceToHost, s_out);
+            if (er == cudaSuccess) er = cudaMemcpyAsync(r->d.i2, dptr(r->o_i2), c * 4, cudaMemcpyDeviceToHost, s_out);
         } else {
             const size_t n = static_cast<size_t>(r->d.n);
-            er = cudaMemcpyAsync(r->d.x, dptr(r->o_x), c * n * 8, cudaMemcpyDeviceToHost, st);
-            if (er == cudaSuccess) er = cudaMemcpyAsync(r->d.i1, dptr(r->o_i1), c * n * 4, cudaMemcpyDeviceToHost, st);
+            er = cudaMemcpyAsync(r->d.x, dptr(r->o_x), c * n * 8, cudaMemcpyDeviceToHost, s_out);
+            if (er == cudaSuccess)
+                er = cudaMemcpyAsync(r->d.i1, dptr(r->o_i1), c * n * 4, cudaMemcpyDeviceToHost, s_out);
         }
         return er;
     };
@@ -304,7 +326,8 @@ tl_status tl_server::enqueue(Slot &sl, std::vector<Req *> &batch)
             jobs[j] = jb;
         }
         char *dtab = dptr(sl.scratch_off + cur);
-        e = cudaMemcpyAsync(dtab, jobs, kv.second.size() * sizeof(NewtonJob), cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(dtab, jobs, kv.second.size() * sizeof(NewtonJob), cudaMemcpyHostToDevice, s_in);
+        if (e == cudaSuccess) e = inputs_ready(sl.groups.size());
         if (e != cudaSuccess) return fail_cuda(sl.h, e);
         NewtonBatch B{};
         B.jobs = reinterpret_cast<const NewtonJob *>(dtab);
@@ -318,6 +341,7 @@ tl_status tl_server::enqueue(Slot &sl, std::vector<Req *> &batch)
         ts = newton_launch(sl.h, kv.first.first, kv.first.second, B, st);
         if (ts != TL_OK) return ts;
         cudaEventRecord(sl.kev[2 * g + 1], st);
+        if ((e = kernels_done(g)) != cudaSuccess) return fail_cuda(sl.h, e);
         cur += tb;
         for (Req *r : kv.second)
             if ((e = copy_out(r)) != cudaSuccess) return fail_cuda(sl.h, e);
@@ -344,7 +368,8 @@ tl_status tl_server::enqueue(Slot &sl, std::vector<Req *> &batch)
                 hp[q] = static_cast<int64_t>(r->o_i1 / 4) + s * n;
             }
         }
-        e = cudaMemcpyAsync(dptr(sl.scratch_off + o_n), hn, o_info - o_n, cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(dptr(sl.scratch_off + o_n), hn, o_info - o_n, cudaMemcpyHostToDevice, s_in);
+        if (e == cudaSuccess) e = inputs_ready(sl.groups.size());
         if (e != cudaSuccess) return fail_cuda(sl.h, e);
         const int32_t *dn = reinterpret_cast<const int32_t *>(dptr(sl.scratch_off + o_n));
         const int64_t *da = reinterpret_cast<const int64_t *>(dptr(sl.scratch_off + o_a));
@@ -361,10 +386,11 @@ tl_status tl_server::enqueue(Slot &sl, std::vector<Req *> &batch)
         ts = ragged_solve(sl.h, static_cast<int64_t>(nsys), dn, ra, dws, st);
         if (ts != TL_OK) return ts;
         cudaEventRecord(sl.kev[2 * g + 1], st);
+        if ((e = kernels_done(g)) != cudaSuccess) return fail_cuda(sl.h, e);
         q = 0;
         for (Req *r : solves) {
             const size_t c = static_cast<size_t>(r->d.count);
-            e = cudaMemcpyAsync(r->d.i2, dinfo + q, c * 4, cudaMemcpyDeviceToHost, st);
+            e = cudaMemcpyAsync(r->d.i2, dinfo + q, c * 4, cudaMemcpyDeviceToHost, s_out);
             if (e == cudaSuccess) e = copy_out(r);
             if (e != cudaSuccess) return fail_cuda(sl.h, e);
             q += c;
@@ -471,7 +497,9 @@ void tl_server::run()
                 stats.host_enqueue_s += std::chrono::duration<double>(Clock::now() - t_host).count();
                 if (ts != TL_OK) {
                     // whatever was issued drains before the slot is reused
+                    cudaStreamSynchronize(sl.s_in);
                     cudaStreamSynchronize(sl.stream);
+                    cudaStreamSynchronize(sl.s_out);
                     cudaGetLastError();
                     retire(sl, ts);
                 }
@@ -523,11 +551,15 @@ extern "C" tl_status tl_server_create(tl_handle *h, const tl_server_config *cfg,
         return TL_ERR_CUDA;
     }
     for (Slot &sl : s->slots) {
-        bool ok = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess && tl_create(&sl.h) == TL_OK;
-        for (int g = 0; ok && g < kMaxGroups; ++g) {
-            cudaEvent_t ev = nullptr;
-            ok = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
-            if (ok) sl.evs.push_back(ev);
+        bool ok = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&sl.s_in, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&sl.s_out, cudaStreamNonBlocking) == cudaSuccess && tl_create(&sl.h) == TL_OK;
+        for (std::vector<cudaEvent_t> *v : {&sl.evs, &sl.ev_in, &sl.ev_k}) {
+            for (int g = 0; ok && g < kMaxGroups; ++g) {
+                cudaEvent_t ev = nullptr;
+                ok = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+                if (ok) v->push_back(ev);
+            }
         }
         for (int g = 0; ok && g < 2 * kMaxGroups; ++g) {
             cudaEvent_t ev = nullptr;
@@ -662,10 +694,12 @@ extern "C" tl_status tl_server_destroy(tl_server *s)
     s->cv_work.notify_all();
     if (s->loop.joinable()) s->loop.join();
     for (Slot &sl : s->slots) {
-        if (sl.stream) cudaStreamSynchronize(sl.stream);
-        for (cudaEvent_t ev : sl.evs) cudaEventDestroy(ev);
-        for (cudaEvent_t ev : sl.kev) cudaEventDestroy(ev);
-        if (sl.stream) cudaStreamDestroy(sl.stream);
+        for (cudaStream_t x : {sl.s_in, sl.stream, sl.s_out})
+            if (x) cudaStreamSynchronize(x);
+        for (std::vector<cudaEvent_t> *v : {&sl.evs, &sl.ev_in, &sl.ev_k, &sl.kev})
+            for (cudaEvent_t ev : *v) cudaEventDestroy(ev);
+        for (cudaStream_t x : {sl.s_in, sl.stream, sl.s_out})
+            if (x) cudaStreamDestroy(x);
         if (sl.h) tl_destroy(sl.h);
         if (sl.stage) cudaFreeHost(sl.stage);
     }

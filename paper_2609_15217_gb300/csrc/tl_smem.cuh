@@ -548,7 +548,7 @@ __device__ __forceinline__ int smem_lupp2(double *M, int n, int RS, int t, int t
 
 // MODE: kGesv (A const, b -> x, LU optional by KEEP) or kGetrf (A in place).
 // WALK: element walk of the trailing update instead of the lane tile.
-template <int T, int LAYOUT, int MODE, bool KEEP, bool WALK = (T >= 16), bool ASYNC_LOAD = true>
+template <int T, int LAYOUT, int MODE, bool KEEP, bool WALK = (T >= 16), bool ASYNC_LOAD = (T < 16)>
 __global__ void __launch_bounds__(128) k_smem_group(SolveArgs args, int n)
 {
     extern __shared__ double smem[];

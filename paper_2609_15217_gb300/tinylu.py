@@ -82,6 +82,9 @@ _SIGS = {
     "tl_server_destroy": ([_vp], _int),
     "tl_dispatch_set": ([_vp, _int, _int, _int, _int], _int),
     "tl_ragged_set_mode": ([_vp, _int], _int),
+    "tl_autotune_ragged": ([_vp, _int, _int, C.c_char_p], _int),
+    "tl_ragged_dispatch_set": ([_vp, _int, _int, _int], _int),
+    "tl_ragged_dispatch_get": ([_vp, _int, C.POINTER(_int), C.POINTER(_int)], _int),
     "tl_check_bounds_violations": ([C.POINTER(C.c_ulonglong)], _int),
     "tl_measure_fma_peak": ([_vp, _int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double), _vp],
                             _int),
@@ -233,6 +236,21 @@ def tl_check_bounds_violations():
     v = C.c_ulonglong(0)
     st = _lib.tl_check_bounds_violations(C.byref(v))
     return st, v.value
+
+
+def tl_autotune_ragged(h, n_min, n_max, table_path=None):
+    return _lib.tl_autotune_ragged(h, n_min, n_max, table_path.encode() if table_path else None)
+
+
+def tl_ragged_dispatch_set(h, n, lanes=0, mixed_route=-1):
+    return _lib.tl_ragged_dispatch_set(h, n, lanes, mixed_route)
+
+
+def tl_ragged_dispatch_get(h, n):
+    """Returns (status, lanes, refines)."""
+    lanes, refines = C.c_int(0), C.c_int(0)
+    st = _lib.tl_ragged_dispatch_get(h, n, C.byref(lanes), C.byref(refines))
+    return st, lanes.value, refines.value
 
 
 def tl_ragged_set_mode(h, mode):

@@ -111,9 +111,21 @@ def test_tanh_parity(tl, h, n):
     tl.check("tanh", tl.tl_newton_integrate(h, law, npts, d_in, d_x, None, d_it, d_st, 1e-10, 20), h)
     torch.cuda.synchronize()
     ok = r["rmin_ratio"] >= 1e-6
-    assert np.array_equal(d_it.cpu().numpy()[ok], r["iterations"][ok])
-    assert np.array_equal(d_st.cpu().numpy()[ok], r["status"][ok])
-    compare_states(d_x.cpu().numpy().T[ok], r["x"][ok])
+    # points whose residual ratio sits within 1e-6 of the threshold may stop
+    # one iteration apart (the law's tanh differs in the last bits between
+    # CUDA and libm): at most one in a thousand, and those still end within
+    # one iteration of the oracle at a converged state
+    flagged = ~ok
+    assert flagged.sum() <= max(1, npts // 1000), flagged.sum()
+    it_g, st_g, x_g = d_it.cpu().numpy(), d_st.cpu().numpy(), d_x.cpu().numpy().T
+    assert np.array_equal(it_g[ok], r["iterations"][ok])
+    assert np.array_equal(st_g[ok], r["status"][ok])
+    compare_states(x_g[ok], r["x"][ok])
+    if flagged.any():
+        assert (np.abs(it_g[flagged] - r["iterations"][flagged]) <= 1).all()
+        assert (st_g[flagged] == 0).all() and (r["status"][flagged] == 0).all()
+        err = np.abs(x_g[flagged] - r["x"][flagged]).max(axis=1) / np.maximum(np.abs(r["x"][flagged]).max(axis=1), 1e-300)
+        assert (err <= 1e-8).all(), err.max()
 
 
 def test_newton_argument_errors(tl, h):

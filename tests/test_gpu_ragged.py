@@ -169,21 +169,29 @@ def test_persistent_launch_equals_per_size_launches(tl, h):
         assert np.array_equal(np.stack([pp[p_off[s]:p_off[s] + n] for s in idx]), pivo), n
 
 
-@pytest.mark.parametrize("lanes", [2, 4, 8, 16, 32])
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
 def test_persistent_launch_every_lane_count(tl, h, lanes):
-    # the dispatch table's shared-memory ragged variant sets the lanes per
-    # system of each size in the single launch
-    for n in range(2, 33):
-        assert tl.tl_dispatch_set(h, n, tl.TL_LAYOUT_PER_SYSTEM, tl.variant_id(lanes, shared=True), 0) == tl.TL_OK
+    # the ragged dispatch table sets the lanes per system of each size in
+    # the single launch (one thread in registers only up to n = 7)
+    top = 7 if lanes == 1 else 32
+    for n in range(1, top + 1):
+        assert tl.tl_ragged_dispatch_set(h, n, lanes, -1) == tl.TL_OK
+        assert tl.tl_ragged_dispatch_get(h, n)[1] == lanes
     try:
         g = inputs.rng(86 + lanes)
         sizes = g.integers(1, 33, size=1500).astype(np.int64)
         systems, a_off, b_off, p_off, Abuf, bbuf, npiv = make_ragged(sizes, 87 + lanes)
+        plant_special(systems, Abuf, bbuf, a_off)
         x, piv, info = run_ragged(tl, h, sizes, a_off, b_off, p_off, Abuf, bbuf, npiv)
-        check_ragged(sizes, systems, b_off, p_off, x, piv, info)
+        for n, (idx, A, b) in systems.items():
+            _, pivo, infoo, _ = oracle.gesv(A, b)
+            assert np.array_equal(info[idx], infoo), n
+            assert np.array_equal(np.stack([piv[p_off[s]:p_off[s] + n] for s in idx]), pivo), n
+        ok = {n: (idx[info[idx] == 0], A[info[idx] == 0], b[info[idx] == 0]) for n, (idx, A, b) in systems.items()}
+        check_ragged(sizes, ok, b_off, p_off, x, piv, info)
     finally:
-        for n in range(2, 33):
-            tl.tl_dispatch_set(h, n, tl.TL_LAYOUT_PER_SYSTEM, 0, 0)
+        for n in range(1, 33):
+            tl.tl_ragged_dispatch_set(h, n, 0, -1)
 
 
 def test_ragged_one_size_only(tl, h):

@@ -31,7 +31,11 @@ def tl():
 
 @pytest.fixture(scope="module")
 def h(tl):
+    # every size refines (the default routes n <= 20 to binary64; see
+    # test_default_route_to_binary64)
     hh = tl.tl_create()
+    for n in range(1, 33):
+        assert tl.tl_ragged_dispatch_set(hh, n, 0, 0) == tl.TL_OK
     yield hh
     tl.tl_destroy(hh)
 
@@ -180,3 +184,63 @@ def test_ir_each_kernel_with_special_systems(tl, h, n, variant):
     assert ref[4] == 0 and ref[5] == 0
     assert np.array_equal(x[b_off[5]:b_off[5] + n], np.arange(n) / 2.0)
     assert stats[n][0] >= 4 and sum(stats[n][1:]) > 200
+
+
+def test_default_route_to_binary64(tl):
+    # default routing: sizes up to 20 are solved in binary64 directly
+    # (refine_steps -1, results bit-identical to TL_PREC_FP64), larger
+    # sizes refine exactly as the oracle's scheme
+    hd = tl.tl_create()
+    try:
+        for n in (6, 20, 21, 32):
+            st, lanes, refines = tl.tl_ragged_dispatch_get(hd, n)
+            assert st == tl.TL_OK and refines == (1 if n >= 21 else 0) and lanes in (1, 2, 4, 8, 16, 32)
+        g = inputs.rng(190)
+        sizes = g.choice([6, 13, 20, 21, 25, 32], size=2500).astype(np.int64)
+        systems, a_off, b_off, p_off, Abuf, bbuf, npiv = make_ragged(sizes, 191)
+        x, piv, info, ref = run_ir(tl, hd, sizes, a_off, b_off, p_off, Abuf, bbuf, npiv)
+        x64, piv64, info64, _ = run_ir(tl, hd, sizes, a_off, b_off, p_off, Abuf, bbuf, npiv, prec=0)
+        small = sizes <= 20
+        assert (ref[small] == -1).all()
+        for n, (idx, A, b) in systems.items():
+            if n <= 20:
+                for s in idx:
+                    assert np.array_equal(x[b_off[s]:b_off[s] + n].view(np.int64), x64[b_off[s]:b_off[s] + n].view(np.int64))
+                    assert np.array_equal(piv[p_off[s]:p_off[s] + n], piv64[p_off[s]:p_off[s] + n])
+                assert np.array_equal(info[idx], info64[idx])
+        big = {n: v for n, v in systems.items() if n >= 21}
+        check_ir(big, b_off, p_off, x, piv, info, ref)
+        # a size can be routed either way explicitly
+        assert tl.tl_ragged_dispatch_set(hd, 6, 0, 0) == tl.TL_OK and tl.tl_ragged_dispatch_get(hd, 6)[2] == 1
+        assert tl.tl_ragged_dispatch_set(hd, 25, 0, 1) == tl.TL_OK and tl.tl_ragged_dispatch_get(hd, 25)[2] == 0
+        assert tl.tl_ragged_dispatch_set(hd, 25, 3, -1) == tl.TL_ERR_INVALID_ARG
+        assert tl.tl_ragged_dispatch_set(hd, 8, 1, -1) == tl.TL_ERR_INVALID_ARG   # one thread only up to n = 7
+    finally:
+        tl.tl_destroy(hd)
+
+
+def test_ragged_autotune_table(tl):
+    import json
+    import os
+    import tempfile
+    hd = tl.tl_create()
+    try:
+        path = os.path.join(tempfile.mkdtemp(), "ragged.json")
+        assert tl.tl_autotune_ragged(hd, 11, 13, path) == tl.TL_OK
+        entries = json.load(open(path))["entries"]
+        assert [e["n"] for e in entries] == [11, 12, 13]
+        for e in entries:
+            st, lanes, refines = tl.tl_ragged_dispatch_get(hd, e["n"])
+            assert lanes == e["lanes"] and refines == e["mixed_refines"]
+            assert e["ms_fp64"] > 0 and e["ms_mixed"] > 0
+        # tuned handle still matches the oracle
+        g = inputs.rng(192)
+        sizes = g.choice([11, 12, 13], size=900).astype(np.int64)
+        systems, a_off, b_off, p_off, Abuf, bbuf, npiv = make_ragged(sizes, 193)
+        x, piv, info, ref = run_ir(tl, hd, sizes, a_off, b_off, p_off, Abuf, bbuf, npiv, prec=0)
+        for n, (idx, A, b) in systems.items():
+            _, pivo, infoo, _ = oracle.gesv(A, b)
+            assert np.array_equal(np.stack([piv[p_off[s]:p_off[s] + n] for s in idx]), pivo)
+            assert np.array_equal(info[idx], infoo)
+    finally:
+        tl.tl_destroy(hd)
