@@ -86,15 +86,17 @@ FP64_PEAK_DERIVED_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12
 
 
 # DRAM bytes per system measured by ncu for the current kernels, keyed by
-# (variant, n) (dram__bytes_read.sum + dram__bytes_write.sum of one launch /
-# systems); an entry must be removed whenever its kernel changes.
-DRAM_BYTES_PER_SYSTEM = {}
+# (variant, n): dram__bytes_read.sum + dram__bytes_write.sum of one launch
+# (ncu flushes the caches before it) / systems in the launch.  An entry must
+# be removed whenever its kernel changes.
+DRAM_BYTES_PER_SYSTEM = {(132, 32): 8783, (116, 28): 6776, (116, 25): 5440, (208, 23): 4685}
 
 VARIANT_NAMES = {1: "k_factor_thread", 2: "k_factor_group<T=2>", 4: "k_factor_group<T=4>",
-                 8: "k_factor_group<T=8>", 16: "k_factor_group<T=16>", 102: "k_smem_group<T=2>",
-                 104: "k_smem_group<T=4>", 108: "k_smem_group<T=8>", 116: "k_smem_group<T=16>",
-                 132: "k_smem_group<T=32>", 202: "k_smem_group<T=2, walk>", 204: "k_smem_group<T=4, walk>",
-                 208: "k_smem_group<T=8, walk>"}
+                 8: "k_factor_group<T=8>", 16: "k_factor_group<T=16>",
+                 102: "k_smem_group<T=2, lane tile>", 104: "k_smem_group<T=4, lane tile>",
+                 108: "k_smem_group<T=8, lane tile>", 116: "k_smem_group<T=16, element walk>",
+                 132: "k_smem_group<T=32, element walk>", 202: "k_smem_group<T=2, element walk>",
+                 204: "k_smem_group<T=4, element walk>", 208: "k_smem_group<T=8, element walk>"}
 
 
 def load_peaks():

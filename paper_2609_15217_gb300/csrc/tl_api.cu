@@ -70,12 +70,24 @@ int default_ir_id(int n)
 
 int default_ragged_id(int n)
 {
-    if (n <= 16) return default_lanes(n);
+    if (n <= 16) return variant_id(default_register_lanes(n), 0);
     return variant_id(n <= 26 ? 16 : 32, 1);
 }
 
-// Default variant id per n before any autotuning.
-int default_lanes(int n) { return variant_id(default_register_lanes(n), 0); }
+// Default gesv/getrf variant id per n before any autotuning: the variant
+// tl_autotune found fastest at each n on a GB300 (interleaved batches of
+// about 1.6 GFLOP per n).  One thread per system in registers up to n = 9,
+// then the two-step element walk in shared memory with 2, 4, 8, 16 and 32
+// lanes per system.
+int default_lanes(int n)
+{
+    if (n <= 9) return variant_id(1, 0);
+    if (n <= 11) return variant_id(2, 2);
+    if (n <= 15) return variant_id(4, 2);
+    if (n <= 23) return variant_id(8, 2);
+    if (n <= 28) return variant_id(16, 1);
+    return variant_id(32, 1);
+}
 
 // Variant by id (lanes + 100 * kind); falls back to the register kernel of
 // the default lane count, then to anything registered.

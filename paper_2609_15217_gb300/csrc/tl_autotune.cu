@@ -326,7 +326,7 @@ extern "C" tl_status tl_autotune_ragged(tl_handle *h, int n_min, int n_max, cons
         float best64 = 1e30f;
         {
             for (int T : {1, 2, 4, 8, 16, 32}) {
-                if (T == 1 && n > kPersistRegMaxN) continue;  // one thread in registers up to n = 7
+                if (T == 1 && n > kPersistRegMaxN) continue;  // one thread in registers: small n only
                 // only choices within the launch's slice: a larger one would
                 // shrink the resident warps of every size in a mixed batch
                 if (persist_need(n, T) > kPersistSliceDoubles) continue;

@@ -180,9 +180,10 @@ __device__ __forceinline__ void persist_item_reg(const RaggedArgs &r, int64_t be
     __syncwarp();  // the next item's copies overwrite the slice
 }
 
-// One warp per block; dynamic shared memory = P.warp_doubles doubles.  12
-// blocks per SM (the slice's occupancy) leave 170 registers per thread.
-__global__ void __launch_bounds__(32, 12) k_ragged_persist(RaggedArgs r, const __grid_constant__ PersistPlan P)
+// One warp per block; dynamic shared memory = P.warp_doubles doubles.
+// kPersistWarps blocks per SM (the slice's occupancy) set the register
+// limit (170 per thread for 12).
+__global__ void __launch_bounds__(32, kPersistWarps) k_ragged_persist(RaggedArgs r, const __grid_constant__ PersistPlan P)
 {
     extern __shared__ double smem[];
     __shared__ int32_t s_start[TL_MAX_N + 1];

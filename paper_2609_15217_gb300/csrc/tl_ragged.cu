@@ -10,6 +10,7 @@
 // as a mode (tl_ragged_set_mode), the comparator of the single launch.  No
 // host synchronization: the bucket sizes stay on the device and every
 // launch reads them there.
+#include <algorithm>
 #include <climits>
 
 #include "tinylu.h"
@@ -136,9 +137,9 @@ size_t ragged_ws_ints(int64_t batch, bool mixed)
 }
 
 // Lanes per system of the single persistent launch for size n when the
-// dispatch table names none: the fastest choice measured on GB300 within
-// the launch's slice of kPersistSliceDoubles (one thread in registers up
-// to n = 7, then 2, 4, 8 and 16 lanes in shared memory).
+// dispatch table names none: the fastest choice measured on GB300 (one
+// thread in registers up to kPersistRegMaxN, then 2, 4, 8 and 16 lanes in
+// shared memory), widened by persist_lanes where it does not fit the slice.
 int default_persist_lanes(int n)
 {
     if (n <= kPersistRegMaxN) return 1;
@@ -171,7 +172,8 @@ int persist_lanes(const tl_handle *h, int n, int limit)
         const int L = id % 100;
         if ((L == 1 && n <= kPersistRegMaxN) || L == 2 || L == 4 || L == 8 || L == 16 || L == 32) T = L;
     }
-    while (T < 32 && static_cast<size_t>(persist_need(n, T)) * sizeof(double) > static_cast<size_t>(limit)) T *= 2;
+    const size_t cap = std::min(static_cast<size_t>(limit), sizeof(double) * kPersistSliceDoubles);
+    while (T < 32 && static_cast<size_t>(persist_need(n, T)) * sizeof(double) > cap) T *= 2;
     return T;
 }
 
@@ -227,7 +229,7 @@ tl_status launch_persist(tl_handle *h, RaggedArgs &r, int32_t *plan, cudaStream_
     const tl_status st = smem_opt_in(h, kern, &limit);
     if (st != TL_OK) return st;
     PersistPlan P{};
-    int need = kPersistSliceDoubles;
+    int need = 0;
     P.lanes[0] = 32;
     for (int n = 1; n <= TL_MAX_N; ++n) {
         const int T = persist_lanes(h, n, limit);
@@ -395,7 +397,7 @@ extern "C" tl_status tl_ragged_dispatch_set(tl_handle *h, int n, int lanes, int 
     if (n < 1 || n > TL_MAX_N) return fail_arg(h, 2);
     if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
         return fail_arg(h, 3);
-    if (lanes == 1 && n > kPersistRegMaxN) return fail_arg(h, 3);  // one thread in registers: n <= 7
+    if (lanes == 1 && n > kPersistRegMaxN) return fail_arg(h, 3);  // one thread in registers: n <= kPersistRegMaxN
     if (mixed_route < -1 || mixed_route > 1) return fail_arg(h, 4);
     h->choice[n][kPerSystem][kOpRagged] = Choice{lanes ? variant_id(lanes, 1) : 0, 0};
     h->mixed_route[n] = static_cast<signed char>(mixed_route);

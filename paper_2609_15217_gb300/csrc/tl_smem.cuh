@@ -2,22 +2,21 @@
 // system, run-time n (<= 32).
 //
 // Each system is an augmented n x (n+1) row-major block in shared memory
-// (column n holds b, then y, then x), rows RS doubles apart.  The
-// interchanges of Sec. 2.2 swap whole rows (L part included) in place, the
-// T lanes sharing the columns.
+// (column n holds b, then y, then x), rows RS doubles apart (RS odd), then
+// n reciprocals and n pivot rows.  The interchanges of Sec. 2.2 swap whole
+// rows in place, the T lanes sharing the columns.
 //
-// Work split: at elimination step k the m = n-k-1 live rows and the n-k live
-// columns (b included) are cut among a TR x TC tile of lanes (2 x 4 for
-// T = 8): lane (tr, tc) keeps its columns of the pivot row in registers and
-// walks its rows, one multiplier per row, so an update costs one shared
-// load and one store; every lane has the same number of live elements up to
-// one row or column.  The column loop stops at a bound that is the same for
-// the whole warp, so no FP64 instruction is issued for a dead column chunk.
-// Loops over rows run at run time, so the code stays small whatever n is.
-// With 16 or 32 lanes per system the trailing block is instead walked
-// element by element, row-major, lane t taking every T-th element: the
-// tile's rounding of rows and columns to the tile shape costs 15-20% of the
-// FP64 instructions there, the element walk none.
+// Two eliminations share this layout:
+//   * smem_lupp2 (the fast path): the trailing block is walked element by
+//     element, lane t taking every T-th element row-major, and the updates
+//     of two elimination steps are applied in one pass; see its comment.
+//   * smem_lupp: one step per pass on a TR x TC tile of lanes (lane (tr, tc)
+//     keeps its columns of the pivot row in registers and walks its rows)
+//     or an element walk; kept for the lane-tile variants.
+// The kernels: k_smem_group (fixed-size batches, both layouts; loads into
+// shared memory by cp.async for 2..8 lanes and by register-staged streaming
+// loads for 16 and 32 lanes, the faster choice measured for each) and
+// k_smem_ragged (one size of a ragged batch, the per-size mode).
 //
 // Arithmetic is the same as the register solvers of tinylu_device.cuh (negated
 // multipliers a_ik * (-RN(1/a_kk)), one FMA per update in increasing k, the
