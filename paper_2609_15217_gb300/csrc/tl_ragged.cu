@@ -10,7 +10,6 @@
 // as a mode (tl_ragged_set_mode), the comparator of the single launch.  No
 // host synchronization: the bucket sizes stay on the device and every
 // launch reads them there.
-#include <algorithm>
 #include <climits>
 
 #include "tinylu.h"
@@ -137,9 +136,11 @@ size_t ragged_ws_ints(int64_t batch, bool mixed)
 }
 
 // Lanes per system of the single persistent launch for size n when the
-// dispatch table names none: the fastest choice measured on GB300 (one
-// thread in registers up to kPersistRegMaxN, then 2, 4, 8 and 16 lanes in
-// shared memory), widened by persist_lanes where it does not fit the slice.
+// dispatch table names none: the fastest choice measured on GB300 within
+// the launch's slice of kPersistSliceDoubles (one thread in registers up
+// to kPersistRegMaxN, then 2, 4, 8 and 16 lanes in shared memory).  A
+// choice set through the dispatch table may need a larger slice: the
+// launch then takes it, with fewer warps resident.
 int default_persist_lanes(int n)
 {
     if (n <= kPersistRegMaxN) return 1;
@@ -172,8 +173,7 @@ int persist_lanes(const tl_handle *h, int n, int limit)
         const int L = id % 100;
         if ((L == 1 && n <= kPersistRegMaxN) || L == 2 || L == 4 || L == 8 || L == 16 || L == 32) T = L;
     }
-    const size_t cap = std::min(static_cast<size_t>(limit), sizeof(double) * kPersistSliceDoubles);
-    while (T < 32 && static_cast<size_t>(persist_need(n, T)) * sizeof(double) > cap) T *= 2;
+    while (T < 32 && static_cast<size_t>(persist_need(n, T)) * sizeof(double) > static_cast<size_t>(limit)) T *= 2;
     return T;
 }
 
@@ -229,7 +229,7 @@ tl_status launch_persist(tl_handle *h, RaggedArgs &r, int32_t *plan, cudaStream_
     const tl_status st = smem_opt_in(h, kern, &limit);
     if (st != TL_OK) return st;
     PersistPlan P{};
-    int need = 0;
+    int need = kPersistSliceDoubles;
     P.lanes[0] = 32;
     for (int n = 1; n <= TL_MAX_N; ++n) {
         const int T = persist_lanes(h, n, limit);
