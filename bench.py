@@ -869,7 +869,9 @@ def main():
         path = os.path.join(ROOT, "_build/autotune_ragged.json")
         tl.check("tl_autotune_ragged", tl.tl_autotune_ragged(h, 1, 32, path), h)
         with open(path) as f:
-            tune["ragged"] = {e["n"]: {"lanes": e["lanes"], "mixed_refines": e["mixed_refines"]}
+            tune["ragged"] = {e["n"]: {"lanes": e["lanes"], "mixed_refines": e["mixed_refines"],
+                                       "ir_variant": e["ir_variant"],
+                                       "ms_fp64": round(e["ms_fp64"], 4), "ms_mixed": round(e["ms_mixed"], 4)}
                               for e in json.load(f)["entries"]}
     t_gen = time.perf_counter()
     data = make_sweep(n_list, 1, rank_seed(1236, rank), device, torch, L, I, args.batch)

@@ -350,9 +350,11 @@ tl_status tl_newton_integrate_cpu_driven(tl_handle *h, const tl_law *law, int64_
  * tl_autotune -- time the candidate kernels (thread-to-system mapping and
  * block size) for every n in [n_min, n_max] and the layout on the current
  * device, and keep the fastest per n in the handle's dispatch table (the
- * "best X" size-aware dispatcher, Sec. 4.1).  table_path nullable: if
- * given, the table is also written there as JSON.  Allocates and frees a
- * temporary device batch; must not run during stream capture.
+ * "best X" size-aware dispatcher, Sec. 4.1) for tl_gesv_batched,
+ * tl_getrf_batched and tl_getrs_batched; the ragged solves keep their own
+ * table (tl_autotune_ragged).  table_path nullable: if given, the table is
+ * also written there as JSON.  Allocates and frees a temporary device batch;
+ * must not run during stream capture.
  */
 tl_status tl_autotune(tl_handle *h, int n_min, int n_max, tl_layout layout,
                       const char *table_path);
@@ -381,8 +383,10 @@ tl_status tl_measure_fma_peak(tl_handle *h, int bits, double *tflops, double *fm
  * [n_min, n_max] on homogeneous batches of the current device (uniform
  * [-1, 1] entries, some 1.6 GFLOP of work per size): the lanes per system
  * of the single persistent binary64 launch (2, 4, 8, 16 or 32; n >= 2) and,
- * for TL_PREC_FP32_IR, whether size n refines a binary32 factorization or
- * goes straight to the binary64 solve (whichever was faster; systems whose
+ * for TL_PREC_FP32_IR, the refinement kernel (the register kernel of its
+ * lane count or the shared-memory warp kernel, whichever is faster) and
+ * whether size n refines a binary32 factorization or goes straight to the
+ * binary64 solve (whichever was faster; systems whose
  * conditioning defeats the refinement fall back to binary64 either way, so
  * workloads with many such systems may prefer binary64 for more sizes).
  * The choices stay in the handle; table_path (nullable) receives them as

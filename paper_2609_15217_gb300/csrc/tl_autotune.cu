@@ -34,6 +34,19 @@ __global__ void k_fill_uniform(double *p, int64_t count, uint64_t seed)
 
 bool op_takes_variant(int op) { return op == kOpGesv || op == kOpGesvLU || op == kOpGetrf; }
 
+// The choice of tl_gesv_batched / tl_getrf_batched for (n, layout), and for
+// tl_getrs_batched the register kernel with the same lane count when there
+// is one.  The ragged solves keep their own table (tl_autotune_ragged).
+void set_gesv_family(tl_handle *h, int n, int layout, int variant, int block)
+{
+    for (int op = 0; op < kOps; ++op)
+        if (op_takes_variant(op)) h->choice[n][layout][op] = Choice{variant, block};
+    const int lanes = variant % 100;
+    const VariantList &lo = registry(n, layout, kOpGetrs);
+    for (int i = 0; i < lo.count; ++i)
+        if (lo.v[i].kind == 0 && lo.v[i].lanes == lanes) h->choice[n][layout][kOpGetrs] = Choice{lanes, 0};
+}
+
 // Tuning batch for size n: about 1.6 GFLOP of algorithmic work (some 2 ms at
 // the rates these kernels reach), never fewer than 512 systems per SM nor
 // more than 2^19: the shared-memory variants only show their speed once
@@ -80,13 +93,12 @@ extern "C" tl_status tl_dispatch_set(tl_handle *h, int n, tl_layout layout, int 
     for (int i = 0; i < l.count; ++i)
         if (variant_id(l.v[i].lanes, l.v[i].kind) == variant) found = true;
     if (!found) return fail_arg(h, 4);
-    for (int op = 0; op < kOps; ++op)
-        if (op_takes_variant(op)) h->choice[n][layout][op] = Choice{variant, block};
-    // getrs and the ragged kernels (binary64 and mixed precision) only exist
-    // as register kernels: take the one with the same lane count when there
-    // is one
+    set_gesv_family(h, n, layout, variant, block);
+    // the ragged kernels (binary64 and mixed precision): the register kernel
+    // with the same lane count, or the shared-memory kernel of the same id,
+    // when there is one
     const int lanes = variant % 100;
-    for (int op : {static_cast<int>(kOpGetrs), static_cast<int>(kOpRagged), static_cast<int>(kOpRaggedIr)}) {
+    for (int op : {static_cast<int>(kOpRagged), static_cast<int>(kOpRaggedIr)}) {
         const VariantList &lo = registry(n, layout, op);
         for (int i = 0; i < lo.count; ++i)
             if (lo.v[i].kind == 0 && lo.v[i].lanes == lanes) h->choice[n][layout][op] = Choice{lanes, 0};
@@ -209,7 +221,7 @@ extern "C" tl_status tl_autotune(tl_handle *h, int n_min, int n_max, tl_layout l
             }
         }
         if (st == TL_OK && best_var) {
-            tl_dispatch_set(h, n, layout, best_var, best_block);
+            set_gesv_family(h, n, layout, best_var, best_block);
             table.push_back(Row{n, best_var, best_block, best_ms});
         }
     }
@@ -288,15 +300,16 @@ extern "C" tl_status tl_autotune_ragged(tl_handle *h, int n_min, int n_max, cons
     // so the slice of the launch is the tuned size's own
     const int mode = h->ragged_mode;
     h->ragged_mode = TL_RAGGED_PERSISTENT;
-    Choice saved[TL_MAX_N + 1];
+    Choice saved[TL_MAX_N + 1], saved_ir[TL_MAX_N + 1];
     signed char saved_route[TL_MAX_N + 1];
     for (int n = 1; n <= TL_MAX_N; ++n) {
         saved[n] = h->choice[n][kPerSystem][kOpRagged];
+        saved_ir[n] = h->choice[n][kPerSystem][kOpRaggedIr];
         saved_route[n] = h->mixed_route[n];
         h->choice[n][kPerSystem][kOpRagged] = Choice{variant_id(n <= kPersistRegMaxN ? 1 : 32, 1), 0};
     }
     struct Row {
-        int n, lanes, refine;
+        int n, lanes, refine, ir_variant;
         float ms64, ms_mixed;
     };
     std::vector<Row> table;
@@ -341,17 +354,33 @@ extern "C" tl_status tl_autotune_ragged(tl_handle *h, int n_min, int n_max, cons
             if (st != TL_OK) break;
             h->choice[n][kPerSystem][kOpRagged] = Choice{variant_id(best_T, 1), 0};
         }
+        // mixed precision: every refinement kernel built for n (the
+        // register kernel of its lane count, the shared-memory warp kernel)
         h->mixed_route[n] = 0;  // refine
-        float ms_mixed = 0.f;
-        if ((st = time_it(true, &ms_mixed)) != TL_OK) break;
+        float ms_mixed = 1e30f;
+        int best_ir = 0;
+        const VariantList &li = registry(n, kPerSystem, kOpRaggedIr);
+        for (int i = 0; i < li.count && st == TL_OK; ++i) {
+            const int id = variant_id(li.v[i].lanes, li.v[i].kind);
+            h->choice[n][kPerSystem][kOpRaggedIr] = Choice{id, 0};
+            float ms = 0.f;
+            if ((st = time_it(true, &ms)) != TL_OK) break;
+            if (ms < ms_mixed) {
+                ms_mixed = ms;
+                best_ir = id;
+            }
+        }
+        if (st != TL_OK) break;
+        h->choice[n][kPerSystem][kOpRaggedIr] = saved_ir[n];
         h->mixed_route[n] = saved_route[n];
         // back to the neutral choice while the other sizes are tuned (the
         // winners are applied together at the end)
         h->choice[n][kPerSystem][kOpRagged] = Choice{variant_id(n <= kPersistRegMaxN ? 1 : 32, 1), 0};
-        table.push_back(Row{n, best_T, ms_mixed < best64 ? 1 : 0, best64, ms_mixed});
+        table.push_back(Row{n, best_T, ms_mixed < best64 ? 1 : 0, best_ir, best64, ms_mixed});
     }
     for (int n = 1; n <= TL_MAX_N; ++n) {
         h->choice[n][kPerSystem][kOpRagged] = saved[n];
+        h->choice[n][kPerSystem][kOpRaggedIr] = saved_ir[n];
         h->mixed_route[n] = saved_route[n];
     }
     h->ragged_mode = mode;
@@ -359,6 +388,7 @@ extern "C" tl_status tl_autotune_ragged(tl_handle *h, int n_min, int n_max, cons
     if (st != TL_OK) return st;
     for (const Row &row : table) {
         if (row.lanes) h->choice[row.n][kPerSystem][kOpRagged] = Choice{variant_id(row.lanes, 1), 0};
+        if (row.ir_variant) h->choice[row.n][kPerSystem][kOpRaggedIr] = Choice{row.ir_variant, 0};
         h->mixed_route[row.n] = static_cast<signed char>(row.refine ? 0 : 1);
     }
     if (table_path) {
@@ -366,9 +396,9 @@ extern "C" tl_status tl_autotune_ragged(tl_handle *h, int n_min, int n_max, cons
         if (!f) return TL_ERR_INVALID_ARG;
         std::fprintf(f, "{\"entries\": [");
         for (size_t i = 0; i < table.size(); ++i)
-            std::fprintf(f, "%s{\"n\": %d, \"lanes\": %d, \"mixed_refines\": %d, \"batch\": %lld, "
-                            "\"ms_fp64\": %.6f, \"ms_mixed\": %.6f}",
-                         i ? ", " : "", table[i].n, table[i].lanes, table[i].refine,
+            std::fprintf(f, "%s{\"n\": %d, \"lanes\": %d, \"mixed_refines\": %d, \"ir_variant\": %d, "
+                            "\"batch\": %lld, \"ms_fp64\": %.6f, \"ms_mixed\": %.6f}",
+                         i ? ", " : "", table[i].n, table[i].lanes, table[i].refine, table[i].ir_variant,
                          static_cast<long long>(tuning_batch(h, table[i].n)), table[i].ms64, table[i].ms_mixed);
         std::fprintf(f, "]}\n");
         std::fclose(f);

@@ -233,6 +233,8 @@ def test_ragged_autotune_table(tl):
             st, lanes, refines = tl.tl_ragged_dispatch_get(hd, e["n"])
             assert lanes == e["lanes"] and refines == e["mixed_refines"]
             assert e["ms_fp64"] > 0 and e["ms_mixed"] > 0
+            # the refinement kernel: the 4-lane register kernel or the warp kernel
+            assert e["ir_variant"] in (4, 132)
         # tuned handle still matches the oracle
         g = inputs.rng(192)
         sizes = g.choice([11, 12, 13], size=900).astype(np.int64)
@@ -242,5 +244,11 @@ def test_ragged_autotune_table(tl):
             _, pivo, infoo, _ = oracle.gesv(A, b)
             assert np.array_equal(np.stack([piv[p_off[s]:p_off[s] + n] for s in idx]), pivo)
             assert np.array_equal(info[idx], infoo)
+        # the tuned refinement kernels, every size refining, against the
+        # oracle's scheme
+        for n in (11, 12, 13):
+            assert tl.tl_ragged_dispatch_set(hd, n, 0, 0) == tl.TL_OK
+        x, piv, info, ref = run_ir(tl, hd, sizes, a_off, b_off, p_off, Abuf, bbuf, npiv)
+        check_ir(systems, b_off, p_off, x, piv, info, ref)
     finally:
         tl.tl_destroy(hd)
