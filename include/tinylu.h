@@ -386,9 +386,10 @@ tl_status tl_measure_fma_peak(tl_handle *h, int bits, double *tflops, double *fm
  * for TL_PREC_FP32_IR, the refinement kernel (the register kernel of its
  * lane count or the shared-memory warp kernel, whichever is faster) and
  * whether size n refines a binary32 factorization or goes straight to the
- * binary64 solve (whichever was faster; systems whose
- * conditioning defeats the refinement fall back to binary64 either way, so
- * workloads with many such systems may prefer binary64 for more sizes).
+ * binary64 solve (refinement only where it was at least 15% faster on the
+ * tuning batch: systems whose conditioning defeats the refinement fall back
+ * to binary64 and pay for both, so workloads with many such systems may
+ * prefer binary64 for more sizes).
  * The choices stay in the handle; table_path (nullable) receives them as
  * JSON.  Allocates and frees a temporary device batch; synchronizes; must
  * not run during stream capture.
