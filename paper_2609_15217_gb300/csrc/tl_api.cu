@@ -78,14 +78,14 @@ int default_ragged_id(int n)
 // tl_autotune found fastest at each n on a GB300 (interleaved batches of
 // about 1.6 GFLOP per n).  One thread per system in registers up to n = 9,
 // then the two-step element walk in shared memory with 2, 4, 8, 16 and 32
-// lanes per system.
+// lanes per system (16 up to n = 30, 32 at n = 31, 32).
 int default_lanes(int n)
 {
     if (n <= 9) return variant_id(1, 0);
     if (n <= 11) return variant_id(2, 2);
     if (n <= 15) return variant_id(4, 2);
     if (n <= 23) return variant_id(8, 2);
-    if (n <= 28) return variant_id(16, 1);
+    if (n <= 30) return variant_id(16, 1);
     return variant_id(32, 1);
 }
 

@@ -312,6 +312,48 @@ __device__ __forceinline__ void smem_pivot_search(const double *M, int RS, int k
         const bool c3 = c2 && ml == maxl;
         cpos = static_cast<int>(__reduce_min_sync(0xffffffffu, c3 ? static_cast<unsigned>(i) : 0xffffffffu));
         cv = TL_SM(M, cpos * RS + k, lim);
+    } else if constexpr (T == 16 || T == 8) {
+        // 32 / T systems per warp: each lane's first maximum over its rows,
+        // then the same three reductions once per group (the lanes of the
+        // other groups contribute the neutral value).  Measured against the
+        // shuffle butterfly below: 2.4-4.4% faster at n = 24..28 with 16
+        // lanes, 0.4-1.6% at n = 18..21 with 8
+        constexpr int G = 32 / T;
+        unsigned long long best = 0;
+        int row = hi;
+        for (int i = lo + t; i < hi; i += T) {
+            const unsigned long long m = dev::mag_bits(TL_SM(M, i * RS + k, lim));
+            if (row == hi || m > best) {
+                best = m;
+                row = i;
+            }
+        }
+        const int grp = static_cast<int>(threadIdx.x & 31u) / T;
+        const bool cand = row < hi;
+        const unsigned mh = static_cast<unsigned>(best >> 32), ml = static_cast<unsigned>(best);
+        unsigned maxh = 0;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const unsigned v = __reduce_max_sync(0xffffffffu, grp == g && cand ? mh : 0u);
+            maxh = grp == g ? v : maxh;
+        }
+        const bool c2 = cand && mh == maxh;
+        unsigned maxl = 0;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const unsigned v = __reduce_max_sync(0xffffffffu, grp == g && c2 ? ml : 0u);
+            maxl = grp == g ? v : maxl;
+        }
+        const bool c3 = c2 && ml == maxl;
+        unsigned rmin = 0;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const unsigned v =
+                __reduce_min_sync(0xffffffffu, grp == g && c3 ? static_cast<unsigned>(row) : 0xffffffffu);
+            rmin = grp == g ? v : rmin;
+        }
+        cpos = static_cast<int>(rmin);
+        cv = TL_SM(M, cpos * RS + k, lim);
     } else {
         unsigned long long best = 0;
         int row = hi;
