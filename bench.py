@@ -89,7 +89,8 @@ FP64_PEAK_DERIVED_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12
 # (variant, n): dram__bytes_read.sum + dram__bytes_write.sum of one launch
 # (ncu flushes the caches before it) / systems in the launch.  An entry must
 # be removed whenever its kernel changes.
-DRAM_BYTES_PER_SYSTEM = {(132, 32): 8783}
+DRAM_BYTES_PER_SYSTEM = {(116, 30): 7747, (116, 29): 7257, (116, 28): 6773, (132, 32): 8783, (208, 23): 4684,
+                         (208, 22): 4300}
 
 VARIANT_NAMES = {1: "k_factor_thread", 2: "k_factor_group<T=2>", 4: "k_factor_group<T=4>",
                  8: "k_factor_group<T=8>", 16: "k_factor_group<T=16>",
