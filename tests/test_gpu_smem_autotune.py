@@ -60,6 +60,32 @@ def test_shared_memory_variants(tl, h, n, lanes, walk):
         assert np.array_equal(piv_g2, piv_o) and np.array_equal(x_g2, x_g, equal_nan=True)
 
 
+@pytest.mark.parametrize("lanes", [2, 4, 8, 16, 32])
+@pytest.mark.parametrize("n", [5, 13, 20, 27, 32])
+def test_walk_pivot_ties(tl, h, n, lanes):
+    """Integer entries in {-2..2}: nearly every column holds several entries
+    of the largest magnitude, so the first-maximum rule (the smallest row
+    among exact ties) decides most pivots; the 8-, 16- and 32-lane walks
+    find it with warp reductions, the others with a shuffle butterfly.
+    Pivots, info and LU bit-identical to the oracle, both layouts."""
+    batch = 2 * 64 + 5
+    g = inputs.rng(8100 + 33 * n + lanes)
+    A = g.integers(-2, 3, size=(batch, n, n)).astype(np.float64)
+    b = g.uniform(-1, 1, size=(batch, n))
+    A[7, :, :] = 1.0               # every candidate of every column tied
+    A[9] = np.eye(n)[::-1] * 2.0   # ties with zeros below
+    x_o, piv_o, info_o, _, LU_o = oracle.gesv(A, b, want_lu=True)
+    vid = tl.variant_id(lanes, shared=True, walk=lanes < 16)
+    for layout in (0, 1):
+        assert tl.tl_dispatch_set(h, n, layout, vid, 0) == tl.TL_OK
+        x_g, piv_g, info_g, LU_g = gpu_gesv(tl, h, A, b, layout)
+        assert np.array_equal(info_g, info_o)
+        assert np.array_equal(piv_g, piv_o)
+        assert np.array_equal(LU_g.view(np.int64), LU_o.view(np.int64))
+        ok = info_o == 0
+        check_solution(A[ok], b[ok], x_g[ok], x_o[ok])
+
+
 @pytest.mark.parametrize("n", [9, 20, 32])
 def test_shared_memory_getrf(tl, h, n):
     from paper_2609_15217_gb300 import layout as L
