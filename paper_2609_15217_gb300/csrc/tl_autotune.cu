@@ -43,6 +43,11 @@ bool op_takes_variant(int op) { return op == kOpGesv || op == kOpGesvLU || op ==
 // slower).
 constexpr float kRefineMargin = 0.85f;
 
+// Timed runs per candidate: the first warms up, the fastest of the others
+// counts.  With 2 timed runs the choice between variants within 1-3% of
+// each other changed from one bench run to the next; 4 narrow that noise.
+constexpr int kTuneReps = 5;
+
 // The choice of tl_gesv_batched / tl_getrf_batched for (n, layout), and for
 // tl_getrs_batched the register kernel with the same lane count when there
 // is one.  The ragged solves keep their own table (tl_autotune_ragged).
@@ -208,7 +213,7 @@ extern "C" tl_status tl_autotune(tl_handle *h, int n_min, int n_max, tl_layout l
                 if (v->kind >= 1 && (block / v->lanes) * smem_sys_bytes(n, v->lanes) + 1024 > static_cast<size_t>(h->max_smem_per_block))
                     continue;
                 float ms_best = 1e30f;
-                for (int rep = 0; rep < 3; ++rep) {
+                for (int rep = 0; rep < kTuneReps; ++rep) {
                     cudaEventRecord(e0, ts);
                     st = launch_variant(h, v, n, block, args, ts);
                     cudaEventRecord(e1, ts);
@@ -331,7 +336,7 @@ extern "C" tl_status tl_autotune_ragged(tl_handle *h, int n_min, int n_max, cons
             RaggedArgs rr = r;
             rr.refine = mixed ? dref : nullptr;
             float best = 1e30f;
-            for (int rep = 0; rep < 3; ++rep) {
+            for (int rep = 0; rep < kTuneReps; ++rep) {
                 cudaEventRecord(e0, ts);
                 const tl_status s2 = ragged_solve(h, S, dn, rr, ws, ts, mixed);
                 cudaEventRecord(e1, ts);
