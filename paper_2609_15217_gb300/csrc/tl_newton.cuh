@@ -14,7 +14,9 @@
 //                          LUpp in registers;
 //   k_newton_tanh<N>       the same for the tanh law, N <= 9;
 //   k_newton_tanh_group<N,T>  T lanes per point (row-cyclic rows, the
-//                          sub-warp LUpp of tinylu_device.cuh), N >= 10.
+//                          sub-warp LUpp of tinylu_device.cuh), N = 10;
+//   k_newton_tanh_smem<T>  (tl_newton_smem.cu) T lanes per point with the
+//                          Jacobian in shared memory, n = 11..32.
 // All are persistent: when a point stops (converged, iteration cap,
 // singular, non-finite) its thread (group) stores the results and takes the
 // next point of its stride, so a lane idles for one solve per point instead

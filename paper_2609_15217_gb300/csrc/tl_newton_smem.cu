@@ -1,12 +1,14 @@
 // tl_newton_smem.cu -- fused per-point Newton integration of the tanh law
-// (Algorithm 2) for 25 <= n <= 32 with the Jacobian in shared memory: one
-// point per warp, the LUpp of the shared-memory solver (smem_lupp, 32 lanes,
-// run-time n).  Per iteration lane i assembles row i of F and J
+// (Algorithm 2) for 11 <= n <= 32 with the Jacobian in shared memory: T
+// lanes per point, 32 / T points per warp, the two-step element-walk LUpp
+// of the shared-memory solver (smem_lupp2, run-time n).  Per iteration
+// lane t of a point's group assembles rows t, t + T, ... of F and J
 // (F_i = sum_j a_ij x_j + c_i tanh(x_i) - b_i with the sum as fma in
 // increasing j; J = A + diag(c .* (1 - tanh^2 x))) into the augmented block
-// [J | -F], the warp factors it and solves for dx, and lane i updates x_i.
-// ||F||_2 is a warp sum of F_i^2.  Persistent: a warp that finishes a point
-// stores it and takes the next one.
+// [J | -F], the warp factors every group's block and solves for dx, and
+// the group updates x.  ||F||_2: each lane's fma sum over its rows, then a
+// butterfly over the group.  Persistent: a group whose point stops stores
+// it and takes the next one of its stride.
 #include <cmath>
 
 #include "tinylu.h"
@@ -20,104 +22,147 @@ namespace {
 
 constexpr int kWarpsPerBlock = 4;
 
-// Smallest n run by this kernel (the sub-warp register kernels take the
-// sizes below it: measured faster up to n = 24, where their 8-lane groups
-// keep eight points per warp; at n = 32 this kernel is 1.23x faster than
-// 16-lane groups).
-#ifndef TL_NEWTON_SMEM_MIN_N
-#define TL_NEWTON_SMEM_MIN_N 25
-#endif
+// Lanes per point of the shared-memory kernel for the tanh law at size n;
+// 0 where the sub-warp register kernel runs (n = 10; n <= 9 runs one
+// thread per point).  Measured on GB300 (points/s over n = 10..32 for
+// every lane count and the register kernels): 4 lanes win at n = 11..14,
+// 8 at 15..22, 16 at 23..28, 32 from 29; 9-56% over the register kernels.
+int newton_smem_lanes(int n)
+{
+    if (n <= 10 || n > TL_MAX_N) return 0;
+    if (n <= 14) return 4;
+    if (n <= 22) return 8;
+    if (n <= 28) return 16;
+    return 32;
+}
 
 // Shared memory per point: the solver's block plus 32 doubles of x.
-__host__ __device__ constexpr int newton_smem_doubles(int n) { return smem_sys_doubles(n, 32) + 32; }
+__host__ __device__ constexpr int newton_smem_doubles(int n, int T) { return smem_sys_doubles(n, T) + 32; }
 
+// T lanes per point, 32 / T points per warp.  Every trip of the loop each
+// group with a live point assembles [J | -F] of its point (lane t the rows
+// t, t + T, ...), the warp factors every group's block with the shared-
+// memory solver (warp-synchronous, so groups without a point factor a
+// stale block and ignore it), and each group updates x, decides, and on a
+// stop stores the point and takes the next one of its stride.
+template <int T>
 __global__ void __launch_bounds__(128) k_newton_tanh_smem(NewtonBatch B, int n)
 {
     extern __shared__ double smem[];
+    constexpr int KM = TL_MAX_N / T;  // row slots per lane
     const int lane = threadIdx.x & 31;
-    const int w = threadIdx.x >> 5;
-    double *M = smem + w * newton_smem_doubles(n);
-    double *xs = M + smem_sys_doubles(n, 32);
+    const int t = lane % T;
+    const int per = newton_smem_doubles(n, T);
+    double *M = smem + (threadIdx.x / T) * per;
+    double *xs = M + smem_sys_doubles(n, T);
     const int RS = smem_row_stride(n);
-    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * kWarpsPerBlock;
-    for (int64_t g = static_cast<int64_t>(blockIdx.x) * kWarpsPerBlock + w; g < B.total; g += nwarps) {
-        const NewtonJob jb = load_job(B, g);
-        const double *in = jb.in;
-        const int64_t np = jb.npoints, p = g - jb.start;
-        const bool mine = lane < n;
-        if (mine) xs[lane] = 0.0;
-        const double ci = mine ? in[(n * n + lane) * np + p] : 0.0;
-        const double bi = mine ? in[(n * n + n + lane) * np + p] : 0.0;
+    const int64_t ngroups = (static_cast<int64_t>(gridDim.x) * blockDim.x) / T;
+    int64_t g = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / T;
+    bool have = g < B.total;
+    const double *in = nullptr;
+    int64_t np = 1, p = 0;
+    double r0 = 0.0;
+    int k = 0;
+    bool fresh = true;
+    while (__any_sync(0xffffffffu, have)) {
+        if (have && fresh) {
+            const NewtonJob jb = load_job(B, g);
+            in = jb.in;
+            np = jb.npoints;
+            p = g - jb.start;
+            for (int i = t; i < n; i += T) xs[i] = 0.0;
+            k = 0;
+        }
         __syncwarp();
-        double r0 = 0.0;
-        int k = 0, st = -1;
-        for (bool fresh = true;; fresh = false) {
-            // assemble row `lane` of [J | -F]
-            double acc = 0.0;
-            const double xi = mine ? xs[lane] : 0.0;
-            const double ti = mine ? tanh(xi) : 0.0;
-            for (int j = 0; j < n; ++j) {
-                const double aij = mine ? in[(j * n + lane) * np + p] : 0.0;
-                acc = fma(aij, xs[j], acc);
-                if (mine) M[lane * RS + j] = (j == lane) ? fma(ci, fma(-ti, ti, 1.0), aij) : aij;
-            }
-            const double Fi = mine ? fma(ci, ti, acc) - bi : 0.0;
-            if (mine) M[lane * RS + n] = dev::neg(Fi);
-            double ss = Fi * Fi;
+        // assemble this lane's rows of [J | -F]
+        double ss = 0.0;
 #pragma unroll
-            for (int off = 16; off >= 1; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
-            const double r = sqrt(ss);
-            if (fresh) r0 = r;
-            st = newton_decide<32>(r, r0, k, B.rtol, B.max_iter);
-            if (st >= 0) break;                        // warp-uniform: r is the same on every lane
-            __syncwarp();
-            const int info = smem_lupp2<32, true, false>(M, n, RS, lane, 0, 0.0);
-            if (info != 0) {
-                st = TL_NEWTON_SINGULAR;
-                break;
+        for (int s = 0; s < KM; ++s) {
+            const int i = t + s * T;
+            if (have && i < n) {
+                const double xi = xs[i];
+                const double ti = tanh(xi);
+                const double ci = in[(n * n + i) * np + p];
+                const double bi = in[(n * n + n + i) * np + p];
+                double acc = 0.0;
+                for (int j = 0; j < n; ++j) {
+                    const double aij = in[(j * n + i) * np + p];
+                    acc = fma(aij, xs[j], acc);
+                    M[i * RS + j] = (j == i) ? fma(ci, fma(-ti, ti, 1.0), aij) : aij;
+                }
+                const double Fi = fma(ci, ti, acc) - bi;
+                M[i * RS + n] = dev::neg(Fi);
+                ss = fma(Fi, Fi, ss);
             }
-            if (mine) xs[lane] = xi + M[lane * RS + n];
-            ++k;
-            __syncwarp();
         }
-        if (mine) jb.x[lane * np + p] = xs[lane];
-        if (lane == 0) {
-            jb.iters[p] = k;
-            jb.status[p] = st;
+#pragma unroll
+        for (int off = T / 2; off >= 1; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
+        const double r = sqrt(ss);
+        if (have && fresh) r0 = r;
+        fresh = false;
+        int st = have ? newton_decide<32>(r, r0, k, B.rtol, B.max_iter) : 0;
+        const bool need = have && st < 0;
+        __syncwarp();
+        if (__any_sync(0xffffffffu, need)) {
+            const int info = smem_lupp2<T, true, false>(M, n, RS, t, 0, 0.0);
+            if (need) {
+                if (info != 0) {
+                    st = TL_NEWTON_SINGULAR;
+                } else {
+                    for (int i = t; i < n; i += T) xs[i] += M[i * RS + n];
+                    ++k;
+                }
+            }
         }
         __syncwarp();
+        if (have && st >= 0) {
+            const NewtonJob jb = load_job(B, g);
+            for (int i = t; i < n; i += T) jb.x[i * np + p] = xs[i];
+            if (t == 0) {
+                jb.iters[p] = k;
+                jb.status[p] = st;
+            }
+            g += ngroups;
+            have = g < B.total;
+            fresh = true;
+        }
     }
 }
 
-}  // namespace
-
-// Shared-memory tanh Newton for n in TL_NEWTON_SMEM_MIN_N..32 (false when n
-// is outside).
-bool newton_tanh_smem_launch(tl_handle *h, int n, const NewtonBatch &B, cudaStream_t stream, tl_status *out)
+template <int T>
+tl_status launch_smem_newton(tl_handle *h, int n, const NewtonBatch &B, cudaStream_t stream)
 {
-    if (n < TL_NEWTON_SMEM_MIN_N || n > TL_MAX_N) return false;
-    const void *kern = reinterpret_cast<const void *>(&k_newton_tanh_smem);
+    const void *kern = reinterpret_cast<const void *>(&k_newton_tanh_smem<T>);
     int limit = 0;
-    tl_status st = smem_opt_in(h, kern, &limit);
-    if (st != TL_OK) {
-        *out = st;
-        return true;
-    }
-    const size_t smem = static_cast<size_t>(kWarpsPerBlock) * newton_smem_doubles(n) * 8;
-    if (smem > static_cast<size_t>(limit)) {
-        *out = TL_ERR_UNSUPPORTED;
-        return true;
-    }
+    const tl_status st = smem_opt_in(h, kern, &limit);
+    if (st != TL_OK) return st;
+    const size_t smem = static_cast<size_t>(32 * kWarpsPerBlock / T) * newton_smem_doubles(n, T) * 8;
+    if (smem > static_cast<size_t>(limit)) return TL_ERR_UNSUPPORTED;
     const int nb = blocks_per_sm(h, kern, 32 * kWarpsPerBlock, smem);
-    const int64_t need = (B.total + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const int64_t per_block = 32 * kWarpsPerBlock / T;
+    const int64_t need = (B.total + per_block - 1) / per_block;
     const int64_t resident = static_cast<int64_t>(nb < 1 ? 1 : nb) * h->sm_count;
     const unsigned grid = static_cast<unsigned>(need < resident ? need : resident);
     NewtonBatch arg = B;
     int n_arg = n;
     void *params[] = {&arg, &n_arg};
     const cudaError_t e = cudaLaunchKernel(kern, dim3(grid), dim3(32 * kWarpsPerBlock), params, smem, stream);
-    *out = e == cudaSuccess ? TL_OK : fail_cuda(h, e);
-    return true;
+    return e == cudaSuccess ? TL_OK : fail_cuda(h, e);
+}
+
+}  // namespace
+
+// Shared-memory tanh Newton for the sizes newton_smem_lanes names (false
+// for the others).
+bool newton_tanh_smem_launch(tl_handle *h, int n, const NewtonBatch &B, cudaStream_t stream, tl_status *out)
+{
+    switch (newton_smem_lanes(n)) {
+    case 4: *out = launch_smem_newton<4>(h, n, B, stream); return true;
+    case 8: *out = launch_smem_newton<8>(h, n, B, stream); return true;
+    case 16: *out = launch_smem_newton<16>(h, n, B, stream); return true;
+    case 32: *out = launch_smem_newton<32>(h, n, B, stream); return true;
+    default: return false;
+    }
 }
 
 }  // namespace tl
