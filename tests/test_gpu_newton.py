@@ -128,6 +128,42 @@ def test_tanh_parity(tl, h, n):
         assert (err <= 1e-8).all(), err.max()
 
 
+@pytest.mark.parametrize("n", [10, 12, 20, 26, 32])
+def test_tanh_status_special_points(tl, h, n):
+    """Stopping statuses through every tanh kernel (register groups at
+    n = 10, shared-memory groups of 4, 8, 16 and 32 lanes above): a
+    non-finite point (status 3), a singular Jacobian at the start (A =
+    -diag(c): status 2), the iteration cap (max_iter 1: status 1), next to
+    ordinary points in the same warps; statuses, counts and converged states
+    as the oracle's."""
+    npts = 200 + 7
+    A, c, b = inputs.tanh_points(n, npts, 950 + n)
+    b[3, n // 2] = np.nan                     # non-finite residual
+    A[8] = -np.diag(c[8])                     # J(0) = A + diag(c) = 0
+    A[40] = -np.diag(c[40])
+    for max_iter in (20, 1):
+        r = oracle.newton_tanh(A, c, b, rtol=1e-10, max_iter=max_iter)
+        Acm = A.transpose(0, 2, 1).reshape(npts, n * n)
+        fields = np.ascontiguousarray(np.concatenate([Acm.T, c.T, b.T], axis=0))
+        d_in = torch.from_numpy(fields).to(DEV)
+        d_x = torch.empty((n, npts), dtype=torch.float64, device=DEV)
+        d_it = torch.empty(npts, dtype=torch.int32, device=DEV)
+        d_st = torch.empty(npts, dtype=torch.int32, device=DEV)
+        law = tl.make_law(tl.TL_LAW_TANH, n)
+        tl.check("tanh", tl.tl_newton_integrate(h, law, npts, d_in, d_x, None, d_it, d_st, 1e-10, max_iter), h)
+        torch.cuda.synchronize()
+        it_g, st_g, x_g = d_it.cpu().numpy(), d_st.cpu().numpy(), d_x.cpu().numpy().T
+        assert st_g[3] == 3 and r["status"][3] == 3
+        assert st_g[8] == 2 and st_g[40] == 2 and r["status"][8] == 2
+        ok = r["rmin_ratio"] >= 1e-6
+        assert np.array_equal(st_g[ok], r["status"][ok])
+        assert np.array_equal(it_g[ok], r["iterations"][ok])
+        conv = ok & (r["status"] == 0)
+        compare_states(x_g[conv], r["x"][conv])
+        if max_iter == 1:
+            assert (st_g == 1).sum() > npts // 2
+
+
 def test_newton_argument_errors(tl, h):
     d = torch.zeros(64, dtype=torch.float64, device=DEV)
     i = torch.zeros(64, dtype=torch.int32, device=DEV)
