@@ -410,6 +410,46 @@ def newton_bench(tl, h, steps, warmup, torch, device, I, seed, peak, npoints=NEW
     return out
 
 
+def tanh_newton_bench(tl, h, steps, warmup, torch, device, I, seed, peak, npoints=1 << 17, sizes=(7, 13, 20, 32)):
+    """The tanh law of the served stream, one size class at a time: the
+    fused kernel's points/s, linear solves/s and the FP64 fraction of the
+    solves alone (flops(n) per solve; the law's assembly is not counted)."""
+    out = {}
+    stream = torch.cuda.current_stream()
+    for n in sizes:
+        fields = I.tanh_points_torch(n, npoints, seed + n, device)
+        x = torch.empty((n, npoints), dtype=torch.float64, device=device)
+        it = torch.empty(npoints, dtype=torch.int32, device=device)
+        st = torch.empty(npoints, dtype=torch.int32, device=device)
+        law = tl.make_law(tl.TL_LAW_TANH, n)
+
+        def run():
+            r = tl.tl_newton_integrate(h, law, npoints, fields, x, None, it, st, 1e-10, 20, stream.cuda_stream)
+            if r != 0:
+                tl.check("tl_newton_integrate", r, h)
+        for _ in range(warmup):
+            run()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        med = statistics.median(ms)
+        solves = int(it.to(torch.int64).sum().item())
+        out[n] = {"points": npoints, "ms": med, "points_per_s": npoints / (med / 1e3),
+                  "mean_iterations": solves / npoints, "solves_per_s": solves / (med / 1e3),
+                  "lu_fp64_frac": solves * flops_per_system(n) / (med / 1e3) / 1e12 / peak,
+                  "converged": int((st == 0).sum().item())}
+        del fields, x, it, st
+        torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------------------
 # ragged batch, binary64 vs binary32 factor + binary64 refinement
 # ---------------------------------------------------------------------------
@@ -971,6 +1011,12 @@ def main():
                                        peak)
         extra["newton"]["points_per_s"] *= world
         torch.cuda.empty_cache()
+        log("newton tanh")
+        extra["newton_tanh"] = tanh_newton_bench(tl, h, max(2, args.steps // 2), 2, torch, device, I,
+                                                 rank_seed(1239, rank), peak)
+        for v in extra["newton_tanh"].values():
+            v["points_per_s"] *= world
+            v["solves_per_s"] *= world
 
     if not args.no_ragged:
         log("ragged batch, binary64 and mixed precision")

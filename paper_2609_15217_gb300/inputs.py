@@ -203,3 +203,18 @@ def norton_points_torch(npoints, seed, device, sig_amp=150.0, eps_amp=1e-3):
     sig0[:, :3] -= sig0[:, :3].mean(dim=1, keepdim=True)
     deps = torch.empty((npoints, 6), dtype=torch.float64, device=device).uniform_(-eps_amp, eps_amp, generator=g)
     return sig0, deps
+
+
+def tanh_points_torch(n, npoints, seed, device):
+    """The tanh-law points of tanh_points on the device, as the field-major
+    input of tl_newton_integrate: rows j*n + i hold a_ij, then c_i, then b_i
+    (npoints columns)."""
+    import torch
+    g = _tgen(seed, device)
+    A = torch.empty((npoints, n, n), dtype=torch.float64, device=device).uniform_(-1.0, 1.0, generator=g)
+    A += n * torch.eye(n, dtype=torch.float64, device=device)
+    c = torch.empty((npoints, n), dtype=torch.float64, device=device).uniform_(0.5, 2.0, generator=g)
+    b = torch.empty((npoints, n), dtype=torch.float64, device=device).uniform_(-3.0, 3.0, generator=g) * n
+    fields = torch.cat([A.transpose(1, 2).reshape(npoints, n * n).t(), c.t(), b.t()], dim=0).contiguous()
+    return fields
+
