@@ -399,7 +399,7 @@ tl_status tl_autotune_ragged(tl_handle *h, int n_min, int n_max, const char *tab
 /*
  * tl_ragged_dispatch_set / tl_ragged_dispatch_get -- per size n: lanes per
  * system of the persistent ragged launch (0 = default: one thread with the
- * system in registers up to n = 7, then 2 lanes at n = 8, 4 up to 14, 8 up
+ * system in registers up to n = 7, then 2 lanes up to n = 10, 4 up to 14, 8 up
  * to 22, 16 above; 1 (n <= 7 only) or 2..32 a power of two) and the
  * mixed-precision route (-1 = default: refine from n = 21 on, binary64
  * below; 0 = refine; 1 = binary64; systems of a size routed to binary64 get

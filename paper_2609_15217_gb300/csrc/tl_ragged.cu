@@ -136,15 +136,15 @@ size_t ragged_ws_ints(int64_t batch, bool mixed)
 }
 
 // Lanes per system of the single persistent launch for size n when the
-// dispatch table names none: the fastest choice measured on GB300 within
-// the launch's slice of kPersistSliceDoubles (one thread in registers up
-// to kPersistRegMaxN, then 2, 4, 8 and 16 lanes in shared memory).  A
-// choice set through the dispatch table may need a larger slice: the
-// launch then takes it, with fewer warps resident.
+// dispatch table names none: the choice tl_autotune_ragged makes on a
+// GB300 within the launch's slice of kPersistSliceDoubles (one thread in
+// registers up to kPersistRegMaxN, 2 lanes up to n = 10, 4 up to 14, 8 up
+// to 22, 16 above).  A choice set through the dispatch table may need a
+// larger slice: the launch then takes it, with fewer warps resident.
 int default_persist_lanes(int n)
 {
     if (n <= kPersistRegMaxN) return 1;
-    if (n <= 8) return 2;
+    if (n <= 10) return 2;
     if (n <= 14) return 4;
     if (n <= 22) return 8;
     return 16;
